@@ -1,0 +1,328 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check uses a closed form, an
+independent route (brute-force quadrature, the dimensional kernel, the O(N^6) direct sum),
+a library routine for a special case, the printed Table 1, or an invariant.
+"""
+
+import os
+
+import numpy as np
+import pytest
+from scipy.special import gamma
+
+from oracle import direct, fast_spectral as fs, kernel, krook_wu, moments, quadrature
+from paper_1903_03056_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- quadrature (Sec. 4)
+
+def _sphere_monomial(a, b, c):
+    """int_{S^2} x^a y^b z^c: 2 G((a+1)/2) G((b+1)/2) G((c+1)/2) / G((a+b+c+3)/2), or 0."""
+    if a % 2 or b % 2 or c % 2:
+        return 0.0
+    return 2.0 * gamma((a + 1) / 2) * gamma((b + 1) / 2) * gamma((c + 1) / 2) / gamma(
+        (a + b + c + 3) / 2)
+
+
+@pytest.mark.parametrize("M,degree", [(6, 3), (12, 5), (32, 5)])
+def test_spherical_design_exact_to_its_degree(M, degree):
+    pts, w = quadrature.spherical_design(M)
+    assert np.allclose(np.linalg.norm(pts, axis=1), 1.0)
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            for c in range(degree + 1 - a - b):
+                got = np.sum(w * pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c)
+                assert abs(got - _sphere_monomial(a, b, c)) < 1e-13, (a, b, c)
+
+
+@pytest.mark.parametrize("M", [6, 12, 32])
+def test_spherical_design_is_antipodal(M):
+    pts, _ = quadrature.spherical_design(M)
+    for p in pts:
+        assert np.min(np.linalg.norm(pts + p, axis=1)) < 1e-14
+
+
+def test_radial_rule_exact_for_polynomials():
+    R = 3.7
+    rho, w = quadrature.gauss_legendre_radial(6, R)
+    for k in range(12):
+        assert abs(np.sum(w * rho ** k) - R ** (k + 1) / (k + 1)) < 1e-12 * R ** (k + 1)
+
+
+# ---------------------------------------------------------------- kernel (Secs. 2-3)
+
+@pytest.mark.parametrize("omega,alpha", [(0.5, 1.0), (0.81, 1.0), (0.74, 1.4), (1.0, 2.0)])
+def test_nondimensional_prefactor_from_dimensional_kernel(omega, alpha):
+    """b of Eq. NVSS equals b_{omega,alpha} u0^{2(1-omega)} / B_0 from the dimensional VSS
+    constant (Sec. 2) and the scaling B_0 of Sec. 3, for arbitrary physical units."""
+    kB, T0, m0, d_ref, T_ref = 1.380649e-23, 273.0, 6.63e-26, 4.11e-10, 300.0
+    mi, mj = 1.3 * m0, 2.9 * m0
+    mu = mi * mj / (mi + mj)
+    b_dim = (d_ref ** 2 / 4.0 * (2.0 * kB * T_ref / mu) ** (omega - 0.5) / gamma(2.5 - omega)
+             * alpha / 2.0 ** (alpha - 1.0))
+    u0 = np.sqrt(2.0 * kB * T0 / m0)
+    B0 = u0 * np.sqrt(1.0 + mi / mj) * np.pi * d_ref ** 2 * (T_ref / T0) ** (omega - 0.5)
+    expected = b_dim * u0 ** (2.0 * (1.0 - omega)) / B0
+    assert abs(kernel.b_vss(mi / m0, mj / m0, omega, alpha) / expected - 1.0) < 1e-12
+
+
+def test_domain_rule_single_species():
+    """For equal masses Eq. domain reduces to 2L = (3 + sqrt 2) S."""
+    L = 7.0
+    assert abs(kernel.support_radius(L, [1.0]) - 2 * L / (3 + np.sqrt(2))) < 1e-14
+    assert abs(kernel.support_radius(L, [2.0, 2.0]) - 2 * L / (3 + np.sqrt(2))) < 1e-14
+
+
+def test_domain_rule_binds_for_worst_pair():
+    L, masses = 7.0, [1.0, 2.1, 4.0]
+    S = kernel.support_radius(L, masses)
+    slack = []
+    for mi in masses:
+        for mj in masses:
+            lhs = 2 * L
+            rhs = (max(4 * mj / (mi + mj), 2) + np.sqrt(1 + mj / mi)) * S + S
+            slack.append(lhs - rhs)
+    assert min(slack) > -1e-12 and abs(min(slack)) < 1e-12
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1.4])
+def test_gain_weight_against_brute_force_sphere(alpha):
+    """F of Eq. GG (closed form for VHS, J0 form for VSS) vs a product rule over g_hat
+    written from the definition."""
+    rng = np.random.default_rng(3)
+    k = rng.integers(-6, 6, size=(20, 3)).astype(float)
+    sigma = rng.normal(size=3)
+    sigma /= np.linalg.norm(sigma)
+    rho, cj, b, omega, L = 2.3, 0.37, 0.11, 0.74, 5.0
+    got = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], rho, sigma, cj, b, omega, alpha, L)
+    ref = direct.gain_weight_by_quadrature(k, rho, sigma, cj, b, omega, alpha, L, 60, 96)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_vss_gain_weight_reduces_to_vhs():
+    k = np.array([[0., 0., 0.], [1., 2., 3.], [-4., 1., 0.]])
+    sigma = np.array([0.0, 0.6, 0.8])
+    vhs = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], 1.7, sigma, 0.5, 0.2, 0.6, 1.0, 4.0)
+    vss = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], 1.7, sigma, 0.5, 0.2, 0.6,
+                             1.0 + 1e-12, 4.0)
+    assert np.max(np.abs(vhs - vss)) < 1e-10 * np.max(np.abs(vhs))
+
+
+@pytest.mark.parametrize("omega,alpha", [(0.5, 1.0), (0.74, 1.4)])
+def test_loss_weight_zero_mode_closed_form(omega, alpha):
+    """G^-(0) = (8 pi^2 2^alpha / alpha) b R^(5-2 omega) / (5 - 2 omega) for a fine radial rule
+    (rho^(4-2 omega) is not a polynomial, so the rule is only accurate, not exact)."""
+    R, b = 4.2, 0.13
+    rho, w = quadrature.gauss_legendre_radial(200, R)
+    got = kernel.loss_weight(np.zeros(1), np.zeros(1), np.zeros(1), rho, w, b, omega, alpha, 5.0)
+    ref = 8 * np.pi ** 2 * 2 ** alpha / alpha * b * R ** (5 - 2 * omega) / (5 - 2 * omega)
+    assert abs(got[0] / ref - 1) < 1e-11
+
+
+# ---------------------------------------------------------------- Fourier series (Sec. 4)
+
+@pytest.mark.parametrize("N", [4, 6, 8, 12])
+def test_coefficients_match_library_fft(N):
+    """f_hat_k = N^-3 sum f(v_n) e^{-i pi k.v_n/L} equals numpy's FFT times the grid phase
+    e^{i pi k (1 - 1/N)} per axis for the cell-centred grid."""
+    L = 3.3
+    f = np.random.default_rng(N).random((N, N, N))
+    got = fs.dft3(f, L)
+    k = fs.modes(N)
+    ph = np.exp(1j * np.pi * k * (1.0 - 1.0 / N))
+    ref = np.fft.fftn(f)[np.ix_(k % N, k % N, k % N)] / N ** 3
+    ref = ref * ph[:, None, None] * ph[None, :, None] * ph[None, None, :]
+    assert np.max(np.abs(got - ref)) < 1e-14 * np.max(np.abs(ref))
+    assert np.max(np.abs(fs.idft3(got, L) - f)) < 1e-13
+
+
+# ---------------------------------------------------------------- fast vs direct (Eq. sum)
+
+@pytest.mark.parametrize("N,alpha,s,M", [(4, 1.0, 2, 6), (6, 1.0, 2, 12), (6, 1.4, 2, 6),
+                                         (4, 1.0, 3, 6), (4, 1.4, 3, 12)])
+def test_fast_method_equals_direct_sum(N, alpha, s, M):
+    masses = [1.0, 2.0, 2.6][:s]
+    prob = fs.make_problem(N, 5.0, masses, omega=0.74, alpha=alpha, M=M, N_rho=3)
+    f = np.random.default_rng(N * 10 + s).random((s, N, N, N))
+    Qf, _ = fs.collision(f, prob)
+    Qd = direct.collision_direct(f, prob)
+    assert np.max(np.abs(Qf - Qd)) < 1e-12 * np.max(np.abs(Qf))
+
+
+def _planted(monkeypatch, what):
+    if what == "swapped_mass_fractions":
+        monkeypatch.setattr(kernel, "mass_fractions", lambda mi, mj: (mj / (mi + mj), mi / (mi + mj)))
+    elif what == "loss_without_sigma_integral":
+        orig = kernel.loss_weight
+        monkeypatch.setattr(kernel, "loss_weight",
+                            lambda *a, **k: orig(*a, **k) * a[-2] / 2.0 ** a[-2])
+    elif what == "conjugated_coefficients":
+        orig = fs.forward_matrix
+        monkeypatch.setattr(fs, "forward_matrix", lambda N, L: np.conj(orig(N, L)))
+    elif what == "gain_weight_at_k_times_ci":
+        orig = kernel.gain_weight
+        monkeypatch.setattr(kernel, "gain_weight",
+                            lambda kx, ky, kz, rho, sig, cj, *r, **k: orig(kx, ky, kz, rho, sig, 1 - cj, *r, **k))
+
+
+@pytest.mark.parametrize("what", ["swapped_mass_fractions", "loss_without_sigma_integral",
+                                  "conjugated_coefficients", "gain_weight_at_k_times_ci"])
+def test_planted_mistakes_are_caught_by_direct_sum(monkeypatch, what):
+    """A plausible mistake planted in the oracle makes the fast-vs-direct pin fail."""
+    prob = fs.make_problem(4, 5.0, [1.0, 2.0], omega=0.74, alpha=1.4, M=6, N_rho=3)
+    f = np.random.default_rng(7).random((2, 4, 4, 4))
+    Qd = direct.collision_direct(f, prob)
+    _planted(monkeypatch, what)
+    Qf, _ = fs.collision(f, prob)
+    assert np.max(np.abs(Qf - Qd)) > 1e-6 * np.max(np.abs(Qd))
+
+
+# ---------------------------------------------------------------- Krook-Wu (Sec. 6.1)
+
+def test_krook_wu_derivative_matches_finite_difference():
+    for m1 in (1.0, 4.0):
+        kw = krook_wu.KrookWu(m1, 1.0)
+        assert abs(kw.condition) < 1e-15
+        v2 = np.linspace(0.0, 12.0, 25)
+        for i in range(2):
+            for t in (0.5, 4.0):
+                h = 1e-5
+                fd = (kw.f(i, t + h, v2) - kw.f(i, t - h, v2)) / (2 * h)
+                ref = kw.df(i, t, v2)
+                assert np.max(np.abs(fd - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_krook_wu_conserves_number_density():
+    """n^(i) = int f^(i) dv stays 1 for all t (radial integral of the closed form)."""
+    kw = krook_wu.KrookWu(2.0, 1.0)
+    r = np.linspace(0, 30, 200001)
+    for i in range(2):
+        for t in (1.0, 4.0):
+            dens = np.trapezoid(4 * np.pi * r * r * kw.f(i, t, r * r), r)
+            assert abs(dens - 1.0) < 1e-10
+
+
+def _table1():
+    rows = {}
+    with open(os.path.join(GOLDEN, "krook_wu_table1.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or line.startswith("N "):
+                continue
+            vals = line.split()
+            rows[(int(vals[0]), int(vals[1]))] = [float(x) for x in vals[2:]]
+    return rows
+
+
+def krook_wu_errors(ratio, N, N_rho, M=6, L=12.0, t=4.0):
+    kw = krook_wu.KrookWu(float(ratio), 1.0)
+    prob = fs.make_problem(N, L, [float(ratio), 1.0], omega=1.0, alpha=1.0, M=M, N_rho=N_rho,
+                           b_override=kw.kernel_prefactors())
+    v = fs.velocity_grid(N, L)
+    vx, vy, vz = np.meshgrid(v, v, v, indexing="ij")
+    v2 = vx * vx + vy * vy + vz * vz
+    f = np.stack([kw.f(0, t, v2), kw.f(1, t, v2)])
+    Q, _ = fs.collision(f, prob)
+    return [np.max(np.abs(Q[i].sum(axis=0) - kw.df(i, t, v2))) for i in range(2)]
+
+
+KW_CASES = [(16, 8, r) for r in (1, 2, 4, 6, 8)] + [(16, 16, 4), (32, 16, 1), (32, 16, 8)]
+
+
+@pytest.mark.parametrize("N,N_rho,ratio", KW_CASES)
+def test_krook_wu_reproduces_table1(N, N_rho, ratio):
+    """Sum_j Q_ij against the exact d_t f^(i): the L-infinity errors of Table 1 are
+    reproduced within a factor of 2 (most within 20%; species 1 is the heavy one, m2 = 1).
+    The design's orientation and the radial truncation are not printed, so the digits are
+    not expected to agree exactly."""
+    col = {1: 0, 2: 2, 4: 4, 6: 6, 8: 8}[ratio]
+    paper = _table1()[(N, N_rho)][col:col + 2]
+    got = krook_wu_errors(ratio, N, N_rho)
+    for g, p in zip(got, paper):
+        assert 0.5 < g / p < 2.0, (got, paper)
+
+
+# ---------------------------------------------------------------- physics (Sec. 2)
+
+def _bimaxwellian(N, L, masses, seed):
+    w = synth.Workload("t", 1, N, L, tuple(masses), 0.5, 1.0, 6, 8, "bimaxwellian", 0.0, seed)
+    return synth.node_distribution(w, 0)
+
+
+def _anisotropic_pair(N, L, masses):
+    return np.stack([
+        synth.maxwellian(N, L, 1.0, np.array([0.3, 0.0, 0.0]), 1.0, masses[0])
+        + synth.maxwellian(N, L, 0.5, np.array([-0.3, 0.2, 0.0]), 0.8, masses[0]),
+        synth.maxwellian(N, L, 1.0, np.array([0.0, 0.3, 0.0]), 1.2, masses[1])])
+
+
+@pytest.fixture(scope="module")
+def resolved_runs():
+    """Q for an anisotropic mixture and for a common-(u, T) Maxwellian mixture at
+    N = 16 and N = 32 on [-6, 6]^3 with the 12-point design (masses 1 and 2, HS)."""
+    masses, L = [1.0, 2.0], 6.0
+    out = {}
+    for N in (16, 32):
+        prob = fs.make_problem(N, L, masses, omega=0.5, M=12, N_rho=N // 2)
+        Q, _ = fs.collision(_anisotropic_pair(N, L, masses), prob)
+        u = np.array([0.1, -0.2, 0.05])
+        f_eq = np.stack([synth.maxwellian(N, L, n, u, 1.0, m) for n, m in zip((0.8, 1.3), masses)])
+        Q_eq, _ = fs.collision(f_eq, prob)
+        out[N] = (Q, Q_eq)
+    return masses, L, out
+
+
+def test_equilibrium_maxwellians_give_small_q_decaying_with_n(resolved_runs):
+    """Maxwellians with a common u and T (different n, m) are equilibria (Sec. 2): Q ~ 0,
+    and the residual falls spectrally with N."""
+    _, _, runs = resolved_runs
+    res = {N: np.max(np.abs(Qe)) / np.max(np.abs(Q)) for N, (Q, Qe) in runs.items()}
+    assert res[32] < 2e-3 and res[32] < 0.05 * res[16], res
+
+
+def test_conservation_residuals_small_and_decaying(resolved_runs):
+    """Eq. consv: per-pair mass, pairwise momentum and energy (with the 1/Kn_ij weights of
+    Eq. NMBE) vanish up to the truncation and quadrature errors, which fall with N."""
+    masses, L, runs = resolved_runs
+    rel = {}
+    for N, (Q, _) in runs.items():
+        r = moments.conservation_residuals(Q, masses, L, kappa=moments.knudsen_weights(masses))
+        rel[N] = (np.max(np.abs(r["mass"]) / r["mass_scale"]),
+                  np.max(np.linalg.norm(r["momentum"], axis=-1) / r["momentum_scale"]),
+                  np.max(np.abs(r["energy"]) / r["energy_scale"]))
+    assert rel[32][0] < 5e-3 and rel[32][1] < 2e-2 and rel[32][2] < 5e-3, rel
+    assert all(a < b for a, b in zip(rel[32], rel[16])), rel
+
+
+def test_h_theorem_sign():
+    N, L, masses = 16, 6.0, [1.0, 2.0]
+    prob = fs.make_problem(N, L, masses, omega=0.5, M=6, N_rho=8)
+    f = _bimaxwellian(N, L, masses, 21)
+    Q, _ = fs.collision(f, prob)
+    H = sum(np.sum(Q[i, j] * np.log(np.maximum(f[i], 1e-300))) for i in range(2) for j in range(2))
+    assert H < 0
+
+
+def test_bilinearity_and_species_relabelling():
+    N, L = 8, 5.0
+    prob = fs.make_problem(N, L, [1.0, 3.0], omega=0.7, M=6, N_rho=4)
+    f = np.random.default_rng(2).random((2, N, N, N))
+    Q, _ = fs.collision(f, prob)
+    Q2, _ = fs.collision(f * np.array([2.0, -0.5])[:, None, None, None], prob)
+    assert np.max(np.abs(Q2[0, 1] - (-1.0) * Q[0, 1])) < 1e-12 * np.max(np.abs(Q))
+    assert np.max(np.abs(Q2[0, 0] - 4.0 * Q[0, 0])) < 1e-12 * np.max(np.abs(Q))
+    prob_sw = fs.make_problem(N, L, [3.0, 1.0], omega=0.7, M=6, N_rho=4)
+    Qs, _ = fs.collision(f[::-1].copy(), prob_sw)
+    assert np.max(np.abs(Qs[::-1, ::-1] - Q)) < 1e-12 * np.max(np.abs(Q))
+
+
+def test_reflection_symmetry():
+    """v_x -> -v_x maps Q to its mirror image (the octahedron and the grid are symmetric)."""
+    N, L = 8, 5.0
+    prob = fs.make_problem(N, L, [1.0, 2.0], omega=0.6, M=6, N_rho=4)
+    f = np.random.default_rng(9).random((2, N, N, N))
+    Q, _ = fs.collision(f, prob)
+    Qr, _ = fs.collision(f[:, ::-1].copy(), prob)
+    assert np.max(np.abs(Qr[:, :, ::-1] - Q)) < 1e-12 * np.max(np.abs(Q))

@@ -1,0 +1,319 @@
+"""Benchmark: collision evaluations per second on the 4096-node N=32^3 two-species VHS batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step evaluates all s^2 collision operators Q_ij at every node of the batch (the whole
+hot path: forward transforms, gain over every radial node and design direction, loss,
+assembly) in one call of the C ABI.  `value` is the FP32 (mixed-precision) path with inputs
+resident in HBM; `fp64` is the plain FP64 path on the same batch; `e2e` times the host-buffer
+entry point with both copies inside the timed region.  Inputs (1.07 GB in, 2.15 GB out) are
+larger than L2.  Under torchrun every rank evaluates its own 4096-node batch (weak scaling,
+no collective on the data path).
+"""
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collision evals/s at N=32^3 mixed-precision vs FP64 plain; p50/p99 stream latency"
+WORKLOAD_KEY = "dg_batch_n32"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload():
+    from paper_1903_03056_gb300 import synth
+    return synth.WORKLOADS[WORKLOAD_KEY]
+
+
+def transforms_per_node(w):
+    """Algorithmic 3D transforms per node: s forward (f), P*N_rho*M inverse (antipodal
+    reuse), (s(s+1)/2)*N_rho forward (sigma-summed VHS products), 2P inverse (gain and loss)."""
+    s, P = w.s, w.s * w.s
+    return s + P * w.N_rho * w.M + (s * (s + 1) // 2) * w.N_rho + 2 * P
+
+
+def flops_per_transform(N):
+    n3 = N ** 3
+    return 5.0 * n3 * np.log2(n3)
+
+
+def config_dict(w):
+    return {"workload": w.name, "batch": w.batch, "N": w.N, "species": w.s,
+            "masses": list(w.masses), "omega": w.omega, "alpha": w.alpha, "L": w.L, "M": w.M,
+            "N_rho": w.N_rho, "inputs": "seeded bi-Maxwellians, 5% multiplicative noise",
+            "l2": "inputs larger than L2 (1.07 GB f + 2.15 GB Q per step)"}
+
+
+# ---- clocks ---------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---- CPU oracle (baseline and reference arm) ----------------------------------------------------
+
+def _oracle_node(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    key, node = args
+    from oracle import fast_spectral as fs
+    from paper_1903_03056_gb300 import synth
+    w = synth.WORKLOADS[key]
+    prob = fs.make_problem(w.N, w.L, list(w.masses), omega=w.omega, alpha=w.alpha, M=w.M,
+                           N_rho=w.N_rho)
+    f = synth.node_distribution(w, node)
+    t0 = time.perf_counter()
+    fs.collision(f, prob)
+    return time.perf_counter() - t0
+
+
+def run_oracle_sample(nodes, workers):
+    """Time the FP64 oracle on `nodes` nodes with a spawn pool of `workers` processes."""
+    ctx = mp.get_context("spawn")
+    env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with ctx.Pool(workers) as pool:
+            pool.map(_oracle_node, [(WORKLOAD_KEY, 0)] * workers)  # import warm-up
+            t0 = time.perf_counter()
+            pool.map(_oracle_node, [(WORKLOAD_KEY, n) for n in nodes])
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in env_backup.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return wall
+
+
+def cpu_baseline(w, cores):
+    nodes = list(range(cores))
+    wall = run_oracle_sample(nodes, cores)
+    return {"value": len(nodes) / wall, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d nodes of the %d-node batch, one per process (FP64 numpy oracle, dense "
+                      "DFT matrices, literal (rho, sigma, pair) loop), %.1f s wall" % (len(nodes), w.batch, wall)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        pass  # the oracle has no state to warm beyond its process pool (warmed inside)
+    times = []
+    nodes_per_step = cores
+    ctx_pool_nodes = [list(range(k * nodes_per_step, (k + 1) * nodes_per_step)) for k in range(args.steps)]
+    for nodes in ctx_pool_nodes:
+        times.append(run_oracle_sample(nodes, cores))
+    per_step = sum(times) / len(times)
+    value = nodes_per_step / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d nodes per step on %d host cores" % (nodes_per_step, cores)},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm ---------------------------------------------------------------------------------
+
+def time_steps(torch, fn, steps, warmup, stream, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms / steps
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1903_03056_gb300 import build, dgfs, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    dgfs.load()
+    w = workload()
+    B = w.batch
+    cores = os.cpu_count() or 1
+
+    # CPU baseline first (spawned pool before heavy GPU work; rank 0, N=1 only)
+    cpu = cpu_baseline(w, cores) if (world == 1 and not args.no_cpu_baseline) else None
+
+    f64 = synth.batch_distribution(w)  # [B, s, N, N, N]
+    stream = torch.cuda.Stream()
+    flops_node = transforms_per_node(w) * flops_per_transform(w.N)
+
+    with torch.cuda.stream(stream):
+        f32 = torch.from_numpy(f64.astype(np.float32)).cuda()
+        Q32 = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    plan32 = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho,
+                       precision="fp32", max_batch=B)
+
+    def step32():
+        plan32.eval_ptr(f32.data_ptr(), Q32.data_ptr(), B, stream)
+
+    with ClockSampler(local) as clk:
+        ms32 = time_steps(torch, step32, args.steps, args.warmup, stream, dist)
+    launches = plan32.launches() * args.steps
+    value = world * B / (ms32 * 1e-3)
+
+    # e2e: host buffers (pinned), copies inside the timed region
+    f_host = torch.from_numpy(f64.astype(np.float32)).pin_memory()
+    Q_host = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        plan32.eval_host(f_host, Q_host, stream)
+
+    ms_e2e = time_steps(torch, step_e2e, max(1, args.steps // 2), 1, stream, dist)
+    e2e = {"value": world * B / (ms_e2e * 1e-3), "unit": "evals/s",
+           "h2d_bytes_per_step": int(f_host.numel() * 4), "d2h_bytes_per_step": int(Q_host.numel() * 4)}
+    del f_host, Q_host
+
+    # FP64 plain path on the same batch
+    fp64 = None
+    if not args.no_fp64:
+        del Q32
+        with torch.cuda.stream(stream):
+            fd = torch.from_numpy(f64).cuda()
+            Qd = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=torch.float64, device="cuda")
+        stream.synchronize()
+        plan64 = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M,
+                           N_rho=w.N_rho, precision="fp64")
+
+        def step64():
+            plan64.eval_ptr(fd.data_ptr(), Qd.data_ptr(), B, stream)
+
+        ms64 = time_steps(torch, step64, args.fp64_steps, 1, stream, dist)
+        fp64 = {"value": world * B / (ms64 * 1e-3), "unit": "evals/s", "ms_per_step": ms64,
+                "steps": args.fp64_steps, "dtype": "f64",
+                "mixed_over_fp64": value / (world * B / (ms64 * 1e-3))}
+        plan64.close()
+
+    if rank == 0:
+        achieved = flops_node * B / (ms32 * 1e-3) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "collision_kernel<float,32>",
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                "flops_per_node": flops_node}
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_dict(w), "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "fp64": fp64}
+        print(json.dumps(line), flush=True)
+    plan32.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,114 @@
+/* dgfs.h -- C ABI of the GB300 fast Fourier spectral collision library.
+ *
+ * The library evaluates the multi-species Boltzmann collision operator
+ *
+ *     Q_ij(f_i, f_j)(v) = int_{R^3} int_{S^2} B_ij [ f_i(v') f_j(v_*') - f_i(v) f_j(v_*) ] dsigma dv_*
+ *
+ * (Sec. 2; nondimensional form Eq. NMCO, kernel Eq. NVSS) for every ordered species pair
+ * (i, j) at every node of a batch, by the fast Fourier spectral method of Sec. 4:
+ * truncated Fourier series on [-L, L]^3 with N^3 modes, the gain weight split of Eq. GG
+ * evaluated with an N_rho-point Gauss-Legendre rule in rho and an M-point spherical design in
+ * sigma (each (rho, sigma) term is a product of two phase-shifted inverse transforms taken
+ * through a forward transform), and the loss term as the convolution of f_i with G^- f_j.
+ * Every DG node is an independent evaluation (Sec. 5.1: the nodal GLL basis makes the
+ * collision tensor diagonal), so a batch is a list of nodes.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      : N points per axis, cell-centred, v_n = -L + (n + 1/2) 2L/N.  Q at the grid
+ *             points depends only on the sampled values of f, not on this offset.
+ * Layouts   : f[batch][s][N][N][N] and Q[batch][s][s][N][N][N] (x slowest, z fastest),
+ *             Q[b][i][j] = Q_ij(f_i, f_j) at node b.  Element type: double for DGFS_FP64
+ *             plans, float for DGFS_FP32 plans.
+ * Ownership : the caller owns f and Q.  f is only read; every element of Q is written.
+ *             The plan owns its tables and its workspace (device memory on the device that
+ *             was current at dgfs_create_plan).
+ * Streams   : device entry points are asynchronous and ordered on the given cudaStream_t
+ *             (NULL = legacy default stream); they never synchronise the device.
+ * Threads   : a plan is not thread-safe; distinct plans may run concurrently on distinct
+ *             streams.
+ * Errors    : 0 on success, a negative DGFS_ERR_* code otherwise; dgfs_strerror() names it.
+ *             Arguments are checked before any work is enqueued.
+ */
+#ifndef DGFS_H
+#define DGFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define DGFS_OK 0
+#define DGFS_ERR_INVALID_ARG (-1)    /* a NULL pointer, a size or a parameter out of range */
+#define DGFS_ERR_UNSUPPORTED_N (-2)  /* N is not one of 4, 6, 8, 12, 16, 24, 32, 48 */
+#define DGFS_ERR_OOM (-3)            /* device or host allocation failed */
+#define DGFS_ERR_BUDGET (-4)         /* batch larger than the plan's max_batch */
+#define DGFS_ERR_CUDA (-5)           /* a CUDA runtime call or kernel launch failed */
+#define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up */
+#define DGFS_ERR_UNSUPPORTED (-7)    /* a valid request this build does not implement */
+
+/* arithmetic of the transforms, products and accumulations */
+#define DGFS_FP64 0
+#define DGFS_FP32 1
+
+typedef struct dgfs_plan_s* dgfs_plan; /* opaque, owned by the library */
+
+/* Plan description.  All arrays are host memory, read during dgfs_create_plan only. */
+typedef struct {
+  int N;                   /* grid points per axis, one of 4, 6, 8, 12, 16, 24, 32, 48 */
+  double L;                /* half width of the velocity domain [-L, L]^3 (Sec. 4), > 0 */
+  int s;                   /* number of species, 1..8 */
+  const double* mass;      /* [s] nondimensional masses m_i / m_0 (Sec. 3), > 0 */
+  const double* omega;     /* [s*s] row-major (i, j): viscosity index omega_ij in [0.5, 1] */
+  const double* alpha;     /* [s*s]: scattering parameter alpha_ij; this build needs 1 (VHS) */
+  const double* b_override;/* nullable [s*s]: kernel prefactor b_ij replacing Eq. NVSS */
+  int M;                   /* sphere points; with sigma == NULL one of 6, 12, 32 */
+  const double* sigma;     /* nullable [M*3]: unit directions of the sphere rule */
+  const double* w_sigma;   /* nullable [M]: its weights (default 4 pi / M each) */
+  int N_rho;               /* Gauss-Legendre points in rho on [0, R], >= 1 */
+  double R;                /* radial truncation; <= 0 selects R = 2S with S from Eq. domain */
+  int precision;           /* DGFS_FP64 or DGFS_FP32 */
+  unsigned flags;          /* reserved, must be 0 */
+  int max_batch;           /* largest batch a host-buffer call will pass (>= 0) */
+} dgfs_plan_desc;
+
+/* Build the tables (Gauss-Legendre rule, design, b_ij of Eq. NVSS, R of Eq. domain, gain
+ * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), all FP64) and the
+ * workspace on the current device.  *out receives the plan.  Synchronous. */
+int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out);
+
+/* Release the plan's device memory.  Waits for the device to finish using it. */
+int dgfs_destroy_plan(dgfs_plan plan);
+
+/* Q = all s^2 collision operators of the batch (Sec. 4), device pointers, stream-ordered.
+ * f_dev: [batch][s][N][N][N], Q_dev: [batch][s][s][N][N][N], element type per precision,
+ * both 16-byte aligned.  batch >= 0 (0 is a no-op).  Calls on one plan must not overlap
+ * in time on the device (the workspace is shared); they do not when issued on one stream. */
+int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batch, void* stream);
+
+/* The same evaluation from host buffers (pinned or pageable): copies f to the device,
+ * evaluates, copies Q back and waits for the stream.  batch <= max_batch, else
+ * DGFS_ERR_BUDGET.  The plan's staging buffers are allocated at the first call. */
+int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, int batch,
+                             void* stream);
+
+/* Device bytes of the plan's tables and workspace (workspace includes host-call staging
+ * for `batch` nodes). */
+int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace);
+
+/* The radial truncation R the plan uses (R = 2S from Eq. domain unless given). */
+int dgfs_plan_radius(dgfs_plan plan, double* R);
+
+/* Kernels enqueued by the most recent evaluation on this plan. */
+int dgfs_plan_launches(dgfs_plan plan, int* launches);
+
+/* Static text naming a return code. */
+const char* dgfs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGFS_H */

@@ -1,0 +1,155 @@
+// extern "C" entry points of libdgfs.so (declared in include/dgfs.h).
+#include <cstdint>
+#include <new>
+
+#include "dgfs_internal.h"
+
+struct dgfs_plan_s {
+  dgfs::Plan plan;
+};
+
+namespace {
+
+// make the plan's device current for the duration of a call
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool aligned16(const void* p) { return (reinterpret_cast<std::uintptr_t>(p) & 15u) == 0; }
+
+int launch(const dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+  const int rc = p.precision == DGFS_FP32 ? dgfs::launch_f32(p, f, Q, batch, st)
+                                          : dgfs::launch_f64(p, f, Q, batch, st);
+  if (rc != DGFS_OK) return rc;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  return DGFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out) {
+  if (!desc || !out) return DGFS_ERR_INVALID_ARG;
+  *out = nullptr;
+  dgfs_plan_s* h = new (std::nothrow) dgfs_plan_s;
+  if (!h) return DGFS_ERR_OOM;
+  dgfs::Plan& p = h->plan;
+  int rc = dgfs::build_plan(desc, p);
+  if (rc == DGFS_OK && cudaGetDevice(&p.device) != cudaSuccess) rc = DGFS_ERR_CUDA;
+  if (rc == DGFS_OK) rc = p.precision == DGFS_FP32 ? dgfs::configure_f32(p) : dgfs::configure_f64(p);
+  if (rc == DGFS_OK) rc = dgfs::upload_plan(p);
+  if (rc != DGFS_OK) {
+    dgfs::free_plan(p);
+    cudaGetLastError();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return DGFS_OK;
+}
+
+int dgfs_destroy_plan(dgfs_plan plan) {
+  if (!plan) return DGFS_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(plan->plan.device);
+    cudaDeviceSynchronize();
+    dgfs::free_plan(plan->plan);
+  }
+  delete plan;
+  return DGFS_OK;
+}
+
+int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batch, void* stream) {
+  if (!plan || batch < 0) return DGFS_ERR_INVALID_ARG;
+  if (batch == 0) return DGFS_OK;
+  if (!f_dev || !Q_dev || !aligned16(f_dev) || !aligned16(Q_dev)) return DGFS_ERR_INVALID_ARG;
+  DeviceGuard g(plan->plan.device);
+  if (!g.ok) return DGFS_ERR_CUDA;
+  const int rc = launch(plan->plan, f_dev, Q_dev, batch, static_cast<cudaStream_t>(stream));
+  plan->plan.last_launches = rc == DGFS_OK ? 1 : 0;
+  return rc;
+}
+
+int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, int batch, void* stream) {
+  if (!plan || batch < 0) return DGFS_ERR_INVALID_ARG;
+  if (batch == 0) return DGFS_OK;
+  if (!f_host || !Q_host) return DGFS_ERR_INVALID_ARG;
+  dgfs::Plan& p = plan->plan;
+  if (batch > p.max_batch) return DGFS_ERR_BUDGET;
+  DeviceGuard g(p.device);
+  if (!g.ok) return DGFS_ERR_CUDA;
+  const size_t n3 = size_t(p.N) * p.N * p.N;
+  const size_t fb = size_t(batch) * p.s * n3 * dgfs::real_size(p);
+  const size_t qb = size_t(batch) * p.s * p.s * n3 * dgfs::real_size(p);
+  if (!p.d_stage_f) {
+    const size_t fmax = size_t(p.max_batch) * p.s * n3 * dgfs::real_size(p);
+    const size_t qmax = fmax * p.s;
+    if (cudaMalloc(&p.d_stage_f, fmax) != cudaSuccess || cudaMalloc(&p.d_stage_Q, qmax) != cudaSuccess) {
+      cudaGetLastError();
+      if (p.d_stage_f) cudaFree(p.d_stage_f);
+      p.d_stage_f = nullptr;
+      p.d_stage_Q = nullptr;
+      return DGFS_ERR_OOM;
+    }
+    p.stage_batch = p.max_batch;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(p.d_stage_f, f_host, fb, cudaMemcpyHostToDevice, st) != cudaSuccess) return DGFS_ERR_CUDA;
+  int rc = launch(p, p.d_stage_f, p.d_stage_Q, batch, st);
+  p.last_launches = rc == DGFS_OK ? 1 : 0;
+  if (rc != DGFS_OK) return rc;
+  if (cudaMemcpyAsync(Q_host, p.d_stage_Q, qb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DGFS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DGFS_ERR_CUDA;
+  return DGFS_OK;
+}
+
+int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace) {
+  if (!plan || batch < 0) return DGFS_ERR_INVALID_ARG;
+  const dgfs::Plan& p = plan->plan;
+  const size_t n3 = size_t(p.N) * p.N * p.N;
+  if (tables) *tables = p.table_bytes;
+  if (workspace)
+    *workspace = p.scratch_bytes + size_t(batch) * (p.s + p.s * p.s) * n3 * dgfs::real_size(p);
+  return DGFS_OK;
+}
+
+int dgfs_plan_radius(dgfs_plan plan, double* R) {
+  if (!plan || !R) return DGFS_ERR_INVALID_ARG;
+  *R = plan->plan.R;
+  return DGFS_OK;
+}
+
+int dgfs_plan_launches(dgfs_plan plan, int* launches) {
+  if (!plan || !launches) return DGFS_ERR_INVALID_ARG;
+  *launches = plan->plan.last_launches;
+  return DGFS_OK;
+}
+
+const char* dgfs_strerror(int code) {
+  switch (code) {
+    case DGFS_OK: return "ok";
+    case DGFS_ERR_INVALID_ARG: return "invalid argument";
+    case DGFS_ERR_UNSUPPORTED_N: return "unsupported grid size N";
+    case DGFS_ERR_OOM: return "out of memory";
+    case DGFS_ERR_BUDGET: return "batch exceeds the plan's max_batch";
+    case DGFS_ERR_CUDA: return "CUDA runtime error";
+    case DGFS_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case DGFS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// Persistent collision kernel: one thread-block cluster per work item (node b, task).
+//
+// For a task (i, j) the cluster evaluates, for every radial node rho_q (Sec. 4):
+//
+//   step A  pencil pass along x: for the entries of one sigma_x group, the spectra
+//           f_hat_i e^{+i pi rho c_j k_x sigma_x / L} and f_hat_j e^{-i pi rho c_i k_x sigma_x / L}
+//           are inverse-transformed along x (the x phase is shared by the group);
+//   step B  plane pass over (y, z): per entry, the y and z phases are applied, the inverse
+//           transforms along y and z finish a_e and b_e on the plane, and
+//           P += w_e a_e b_e accumulates in registers; after the last group P is transformed
+//           forward along z and y;
+//   step C  pencil pass along x: forward transform of P, then Q_hat^+_(ij) += w_rho F^(ij) P_hat
+//           (and Q_hat^+_(ji) += w_rho F^(ji) P_hat for a cross pair).
+//
+// then finishes Q_ij = Re IFFT(Q_hat^+_ij) - f_i Re IFFT(G^(ij)- f_hat_j) (the loss
+// convolution of Sec. 4) and writes it.  The 3D transforms are split into a pencil pass
+// (x, strided by N^2) and a plane pass (y, z, contiguous), each line transformed in the
+// registers of one thread; the planes of a volume are spread over the cluster's CTAs and the
+// pencils likewise, with the volumes in an L2-resident per-cluster workspace and cluster
+// barriers between passes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dgfs_internal.h"
+#include "fft_line.cuh"
+
+namespace dgfs {
+
+// compile-time launch shape per (precision, N): cluster size and plane groups per CTA
+template <typename T, int N> struct Shape;
+#define DGFS_SHAPE(TT, NN, CC, GG)                                   \
+  template <> struct Shape<TT, NN> {                                 \
+    static constexpr int cluster = CC;                               \
+    static constexpr int groups = GG;                                \
+  };
+DGFS_SHAPE(float, 4, 1, 4)
+DGFS_SHAPE(float, 6, 1, 6)
+DGFS_SHAPE(float, 8, 1, 8)
+DGFS_SHAPE(float, 12, 1, 12)
+DGFS_SHAPE(float, 16, 1, 16)
+DGFS_SHAPE(float, 24, 2, 12)
+DGFS_SHAPE(float, 32, 4, 8)
+DGFS_SHAPE(float, 48, 4, 3)
+DGFS_SHAPE(double, 4, 1, 4)
+DGFS_SHAPE(double, 6, 1, 6)
+DGFS_SHAPE(double, 8, 1, 8)
+DGFS_SHAPE(double, 12, 1, 12)
+DGFS_SHAPE(double, 16, 1, 8)
+DGFS_SHAPE(double, 24, 2, 6)
+DGFS_SHAPE(double, 32, 4, 4)
+DGFS_SHAPE(double, 48, 4, 1)
+#undef DGFS_SHAPE
+
+template <typename T, int N>
+struct Geo {
+  static constexpr int N2 = N * N;
+  static constexpr int N3 = N * N * N;
+  static constexpr int PITCH = N + 1;  // padded smem row (complex elements)
+  // P accumulates in registers when a second line of N complex values still fits
+  static constexpr bool PREG = (sizeof(T) == 4 && N <= 32) || N <= 16;
+  static constexpr int NBUF = PREG ? 2 : 3;  // smem rows per plane group: T, A, (P)
+  static constexpr int CL = Shape<T, N>::cluster;
+  static constexpr int GP = Shape<T, N>::groups;
+  static constexpr int THREADS = GP * N;
+  static constexpr int PLANES = N / CL;       // planes per CTA
+  static constexpr int PENCILS = N2 / CL;     // pencils per CTA
+  static_assert(PLANES % GP == 0, "planes must split evenly over plane groups");
+  static_assert(N2 % CL == 0, "pencils must split evenly over the cluster");
+  static constexpr size_t SMEM = size_t(GP) * NBUF * N * PITCH * sizeof(C<T>);
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+template <int CL>
+__device__ __forceinline__ void cluster_sync() {
+  if constexpr (CL == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+}
+
+// workspace loads/stores go to L2 only: the data is written by other SMs of the cluster
+template <typename T> __device__ __forceinline__ C<T> ld2(const C<T>* p) { return __ldcg(p); }
+template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __stcg(p, v); }
+
+template <typename T> __device__ __forceinline__ C<T> ldphase(const C<T>* p) { return __ldg(p); }
+
+// transpose a plane held as column t (x[r] = V[r][t]) into row t (x[c] = V[t][c]) and back
+template <typename T, int N>
+__device__ __forceinline__ void cols_to_rows(C<T> (&x)[N], C<T>* tb, int t) {
+  constexpr int P = N + 1;
+#pragma unroll
+  for (int r = 0; r < N; ++r) tb[r * P + t] = x[r];
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < N; ++c) x[c] = tb[t * P + c];
+  __syncthreads();
+}
+template <typename T, int N>
+__device__ __forceinline__ void rows_to_cols(C<T> (&x)[N], C<T>* tb, int t) {
+  constexpr int P = N + 1;
+#pragma unroll
+  for (int c = 0; c < N; ++c) tb[t * P + c] = x[c];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < N; ++r) x[r] = tb[r * P + t];
+  __syncthreads();
+}
+
+template <typename T, int N>
+__device__ __forceinline__ const C<T>* phase_ptr(const KernelParams& p, int task, int q, int e,
+                                                  int role, int axis) {
+  const C<T>* ph = reinterpret_cast<const C<T>*>(p.phase);
+  return ph + ((((size_t(task) * p.n_rho + q) * p.max_ent + e) * 2 + role) * 3 + axis) * N;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const KernelParams p) {
+  using G = Geo<T, N>;
+  using CT = C<T>;
+  constexpr int N2 = G::N2, N3 = G::N3, CL = G::CL, GP = G::GP, NT = G::THREADS;
+  constexpr int PITCH = G::PITCH;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int grp = tid / N;  // plane group
+  const int t = tid % N;    // line within the plane group
+  CT* tb = reinterpret_cast<CT*>(smem_raw) + size_t(grp) * G::NBUF * N * PITCH;
+  CT* ab = tb + N * PITCH;
+  CT* pb = ab + N * PITCH;  // used only when !PREG
+
+  const int rank = CL == 1 ? 0 : int(cluster_rank());
+  const int cid = blockIdx.x / CL;
+  const int n_clusters = gridDim.x / CL;
+  CT* scr = reinterpret_cast<CT*>(p.scratch) + size_t(cid) * 7 * N3;
+  CT* const FI = scr;
+  CT* const FJ = scr + N3;
+  CT* const HA = scr + 2 * N3;
+  CT* const HB = scr + 3 * N3;
+  CT* const PV = scr + 4 * N3;
+  CT* const QA = scr + 5 * N3;
+  CT* const QB = scr + 6 * N3;
+  const int plane0 = rank * G::PLANES;
+  const int pencil0 = rank * G::PENCILS;
+  const T inv_n3 = T(1) / T(N3);
+
+  const int n_items = p.batch * p.n_tasks;
+  for (int item = cid; item < n_items; item += n_clusters) {
+    const int b = item / p.n_tasks;
+    const int task = item % p.n_tasks;
+    const TaskDesc tk = p.tasks[task];
+    const T* fb = reinterpret_cast<const T*>(p.f) + size_t(b) * p.s * N3;
+    const int nspec = tk.j == tk.i ? 1 : 2;
+
+    // ---- step 0: Fourier coefficients f_hat = N^-3 FFT(f) of species i (and j) ----------
+    for (int xl = grp; xl < G::PLANES; xl += GP) {
+      const int x = plane0 + xl;
+      for (int sp = 0; sp < nspec; ++sp) {
+        const T* src = fb + size_t(sp == 0 ? tk.i : tk.j) * N3 + size_t(x) * N2;
+        CT v[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = mk<T>(__ldg(src + t * N + c), T(0));
+        fft_line<T, N, -1>(v);
+        rows_to_cols<T, N>(v, tb, t);
+        fft_line<T, N, -1>(v);
+        CT* dst = (sp == 0 ? FI : FJ) + size_t(x) * N2;
+#pragma unroll
+        for (int r = 0; r < N; ++r) st2<T>(dst + r * N + t, v[r]);
+      }
+    }
+    cluster_sync<CL>();
+    for (int u = tid; u < nspec * G::PENCILS; u += NT) {
+      const int sp = u / G::PENCILS;
+      const int pp = pencil0 + u % G::PENCILS;
+      CT* vol = sp == 0 ? FI : FJ;
+      CT v[N];
+#pragma unroll
+      for (int n = 0; n < N; ++n) v[n] = ld2<T>(vol + n * N2 + pp);
+      fft_line<T, N, -1>(v);
+#pragma unroll
+      for (int n = 0; n < N; ++n) st2<T>(vol + n * N2 + pp, scale<T>(v[n], inv_n3));
+    }
+    cluster_sync<CL>();
+    const CT* FJs = nspec == 2 ? FJ : FI;
+
+    // ---- gain: radial nodes, sigma_x groups, entries ----------------------------------------
+    for (int q = 0; q < p.n_rho; ++q) {
+      for (int gi = 0; gi < tk.n_grp; ++gi) {
+        const GroupDesc gd = p.groups[tk.grp_off + gi];
+        // step A: x-pencils with the group's shared x phase
+        for (int u = tid; u < 2 * G::PENCILS; u += NT) {
+          const int role = u / G::PENCILS;
+          const int pp = pencil0 + u % G::PENCILS;
+          const CT* src = role == 0 ? FI : FJs;
+          const CT* ph = phase_ptr<T, N>(p, task, q, gd.first, role, 0);
+          CT v[N];
+#pragma unroll
+          for (int n = 0; n < N; ++n) v[n] = cmul<T>(ld2<T>(src + n * N2 + pp), ldphase<T>(ph + n));
+          fft_line<T, N, +1>(v);
+          CT* dst = role == 0 ? HA : HB;
+#pragma unroll
+          for (int n = 0; n < N; ++n) st2<T>(dst + n * N2 + pp, v[n]);
+        }
+        cluster_sync<CL>();
+        // step B: (y, z) planes
+        const bool last = gi == tk.n_grp - 1;
+        for (int xl = grp; xl < G::PLANES; xl += GP) {
+          const int x = plane0 + xl;
+          CT P[G::PREG ? N : 1];
+          if constexpr (G::PREG) {
+#pragma unroll
+            for (int c = 0; c < N; ++c) P[c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+          } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) pb[t * PITCH + c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+          }
+          for (int e = gd.first; e < gd.first + gd.count; ++e) {
+            const T w = T(p.ent_w[tk.ent_off + e]);
+            CT v[N];
+            for (int role = 0; role < 2; ++role) {
+              const CT* vol = (role == 0 ? HA : HB) + size_t(x) * N2;
+              const CT* phy = phase_ptr<T, N>(p, task, q, e, role, 1);
+              const CT* phz = phase_ptr<T, N>(p, task, q, e, role, 2);
+#pragma unroll
+              for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), ldphase<T>(phy + r));
+              fft_line<T, N, +1>(v);
+              cols_to_rows<T, N>(v, tb, t);
+#pragma unroll
+              for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], ldphase<T>(phz + c));
+              fft_line<T, N, +1>(v);
+              if (role == 0) {
+#pragma unroll
+                for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
+              }
+            }
+            if constexpr (G::PREG) {
+#pragma unroll
+              for (int c = 0; c < N; ++c) {
+                const CT a = ab[t * PITCH + c];
+                const CT ab_ = cmul<T>(a, v[c]);
+                P[c] = mk<T>(P[c].x + w * ab_.x, P[c].y + w * ab_.y);
+              }
+            } else {
+#pragma unroll
+              for (int c = 0; c < N; ++c) {
+                const CT a = ab[t * PITCH + c];
+                const CT ab_ = cmul<T>(a, v[c]);
+                const CT o = pb[t * PITCH + c];
+                pb[t * PITCH + c] = mk<T>(o.x + w * ab_.x, o.y + w * ab_.y);
+              }
+            }
+          }
+          if (last) {
+            CT v[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+              if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
+            }
+            fft_line<T, N, -1>(v);
+            rows_to_cols<T, N>(v, tb, t);
+            fft_line<T, N, -1>(v);
+#pragma unroll
+            for (int r = 0; r < N; ++r) st2<T>(PV + x * N2 + r * N + t, v[r]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+              CT val;
+              if constexpr (G::PREG) val = P[c]; else val = pb[t * PITCH + c];
+              st2<T>(PV + x * N2 + c * N + t, val);
+            }
+          }
+        }
+        cluster_sync<CL>();
+      }
+      // step C: forward transform of P along x, weight, accumulate
+      for (int u = tid; u < G::PENCILS; u += NT) {
+        const int pp = pencil0 + u;
+        CT v[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) v[n] = ld2<T>(PV + n * N2 + pp);
+        fft_line<T, N, -1>(v);
+        for (int o = 0; o < 2; ++o) {
+          const int pair = o == 0 ? tk.out0 : tk.out1;
+          if (pair < 0) break;
+          const double* Fw = p.Fw + (size_t(pair) * p.n_rho + q) * N3;
+          CT* acc = o == 0 ? QA : QB;
+#pragma unroll
+          for (int n = 0; n < N; ++n) {
+            const T fw = T(__ldg(Fw + n * N2 + pp));
+            CT val = scale<T>(v[n], fw);
+            if (q > 0) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
+            st2<T>(acc + n * N2 + pp, val);
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- finish: Q_ij = Re IFFT(Q_hat^+) - f_i Re IFFT(G^- f_hat_j) --------------------------
+    for (int o = 0; o < 2; ++o) {
+      const int pair = o == 0 ? tk.out0 : tk.out1;
+      if (pair < 0) break;
+      const int io = o == 0 ? tk.i : tk.j;
+      const int jo = o == 0 ? tk.j : tk.i;
+      const CT* acc = o == 0 ? QA : QB;
+      const CT* Fj = jo == tk.i ? FI : FJs;
+      const double* Gm = p.Gm + size_t(pair) * N3;
+      for (int u = tid; u < G::PENCILS; u += NT) {
+        const int pp = pencil0 + u;
+        CT v[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) v[n] = ld2<T>(acc + n * N2 + pp);
+        fft_line<T, N, +1>(v);
+#pragma unroll
+        for (int n = 0; n < N; ++n) st2<T>(HA + n * N2 + pp, v[n]);
+#pragma unroll
+        for (int n = 0; n < N; ++n) v[n] = scale<T>(ld2<T>(Fj + n * N2 + pp), T(__ldg(Gm + n * N2 + pp)));
+        fft_line<T, N, +1>(v);
+#pragma unroll
+        for (int n = 0; n < N; ++n) st2<T>(HB + n * N2 + pp, v[n]);
+      }
+      cluster_sync<CL>();
+      T* Qout = reinterpret_cast<T*>(p.Q) + ((size_t(b) * p.s + io) * p.s + jo) * N3;
+      const T* fi = fb + size_t(io) * N3;
+      for (int xl = grp; xl < G::PLANES; xl += GP) {
+        const int x = plane0 + xl;
+        CT v[N];
+        T gain[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA + x * N2 + r * N + t);
+        fft_line<T, N, +1>(v);
+        cols_to_rows<T, N>(v, tb, t);
+        fft_line<T, N, +1>(v);
+#pragma unroll
+        for (int c = 0; c < N; ++c) gain[c] = v[c].x;
+#pragma unroll
+        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB + x * N2 + r * N + t);
+        fft_line<T, N, +1>(v);
+        cols_to_rows<T, N>(v, tb, t);
+        fft_line<T, N, +1>(v);
+        // row t of this plane; stage through shared memory for a coalesced store
+        T* rb = reinterpret_cast<T*>(tb);
+#pragma unroll
+        for (int c = 0; c < N; ++c) rb[t * PITCH + c] = gain[c] - __ldg(fi + x * N2 + t * N + c) * v[c].x;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < N; ++r) Qout[x * N2 + r * N + t] = rb[r * PITCH + t];
+        __syncthreads();
+      }
+      cluster_sync<CL>();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T, int N>
+int configure_impl(Plan& pl) {
+  using G = Geo<T, N>;
+  auto kern = collision_kernel<T, N>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM)) != cudaSuccess)
+    return DGFS_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G::CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(G::CL);
+  cfg.blockDim = dim3(G::THREADS);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters <= 0) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  pl.shape.cluster = G::CL;
+  pl.shape.groups = G::GP;
+  pl.shape.threads = G::THREADS;
+  pl.shape.smem = G::SMEM;
+  pl.shape.clusters = clusters;
+  pl.scratch_bytes = size_t(clusters) * 7 * G::N3 * sizeof(C<T>);
+  return DGFS_OK;
+}
+
+template <typename T, int N>
+int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t st) {
+  using G = Geo<T, N>;
+  KernelParams kp;
+  kp.f = f;
+  kp.Q = Q;
+  kp.batch = batch;
+  kp.s = pl.s;
+  kp.n_tasks = int(pl.tasks.size());
+  kp.n_rho = pl.N_rho;
+  kp.max_ent = pl.max_ent;
+  kp.tasks = pl.d_tasks;
+  kp.groups = pl.d_groups;
+  kp.ent_w = pl.d_ent_w;
+  kp.phase = pl.d_phase;
+  kp.Fw = pl.d_Fw;
+  kp.Gm = pl.d_Gm;
+  kp.scratch = pl.d_scratch;
+  const int items = batch * kp.n_tasks;
+  const int clusters = items < pl.shape.clusters ? items : pl.shape.clusters;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G::CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(clusters * G::CL);
+  cfg.blockDim = dim3(G::THREADS);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, collision_kernel<T, N>, kp) != cudaSuccess) return DGFS_ERR_CUDA;
+  return DGFS_OK;
+}
+
+#define DGFS_DISPATCH(T, N_, CALL) \
+  switch (N_) {                    \
+    case 4: return CALL(T, 4);     \
+    case 6: return CALL(T, 6);     \
+    case 8: return CALL(T, 8);     \
+    case 12: return CALL(T, 12);   \
+    case 16: return CALL(T, 16);   \
+    case 24: return CALL(T, 24);   \
+    case 32: return CALL(T, 32);   \
+    case 48: return CALL(T, 48);   \
+    default: return DGFS_ERR_UNSUPPORTED_N; \
+  }
+
+}  // namespace dgfs

@@ -1,0 +1,102 @@
+// Internal plan and kernel-parameter structures shared by the host plan builder, the
+// kernel launchers and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dgfs.h"
+
+namespace dgfs {
+
+// One unit of gain work: the product sum P_rho(v) = sum_e w_e a_e(v) b_e(v) over the entries
+// e of the task, where a_e is f_i shifted by +rho c_j sigma_e and b_e is f_j shifted by
+// -rho c_i sigma_e (Sec. 4, the gain formula after Eq. GG).  out0 = i*s+j always receives
+// F^(ij) P_hat; out1 = j*s+i (or -1) receives F^(ji) P_hat, which is exact when the sphere
+// rule is antipodal with equal weights on antipodes, since then P^(ji) = P^(ij).
+struct TaskDesc {
+  int i, j;
+  int out0, out1;
+  int ent_off, n_ent;  // entries (sigma, weight) of this task
+  int grp_off, n_grp;  // groups of entries sharing sigma_x
+};
+
+struct GroupDesc {
+  int first, count;  // entry range within the task, all with the same sigma_x
+};
+
+struct KernelParams {
+  const void* f;          // [batch][s][N^3] real
+  void* Q;                // [batch][s][s][N^3] real
+  int batch, s, n_tasks, n_rho, max_ent;
+  const TaskDesc* tasks;
+  const GroupDesc* groups;
+  const double* ent_w;    // [entries] sigma weight (x2 for halved self pairs)
+  const void* phase;      // complex: [task][rho][max_ent][role 2][axis 3][N]
+  const double* Fw;       // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3
+  const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
+  void* scratch;          // complex: [clusters][7][N^3]
+};
+
+struct LaunchShape {
+  int cluster = 1;        // CTAs cooperating on one work item
+  int groups = 1;         // plane groups per CTA
+  int threads = 0;        // groups * N
+  size_t smem = 0;        // dynamic shared memory per CTA
+  int clusters = 0;       // resident clusters (persistent grid)
+};
+
+struct Plan {
+  int device = 0;
+  int N = 0;
+  double L = 0;
+  int s = 0;
+  int M = 0;
+  int N_rho = 0;
+  double R = 0;
+  int precision = DGFS_FP64;
+  unsigned flags = 0;
+  int max_batch = 0;
+  std::vector<double> mass, omega, alpha, b, sigma, w_sigma, rho, w_rho;
+
+  std::vector<TaskDesc> tasks;
+  std::vector<GroupDesc> groups;
+  std::vector<double> ent_w;
+  std::vector<int> ent_sigma;   // design index of each entry
+  int max_ent = 0;
+
+  // device tables
+  double* d_Fw = nullptr;
+  double* d_Gm = nullptr;
+  double* d_ent_w = nullptr;
+  void* d_phase = nullptr;
+  TaskDesc* d_tasks = nullptr;
+  GroupDesc* d_groups = nullptr;
+  size_t table_bytes = 0;
+
+  // workspace
+  LaunchShape shape;
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* d_stage_f = nullptr;
+  void* d_stage_Q = nullptr;
+  int stage_batch = 0;
+  int last_launches = 0;
+};
+
+size_t real_size(const Plan& p);
+
+// host plan construction (plan.cpp)
+int build_plan(const dgfs_plan_desc* d, Plan& p);
+int upload_plan(Plan& p);
+void free_plan(Plan& p);
+
+// kernel configuration and launch, per precision (collision_f32.cu / collision_f64.cu)
+int configure_f32(Plan& p);
+int configure_f64(Plan& p);
+int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+
+}  // namespace dgfs

@@ -1,0 +1,363 @@
+// Host-side plan construction: quadrature, kernel prefactors, truncation radius, the
+// FP64 gain/loss weight tables and the per-task phase tables (Secs. 3-4).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+
+#include "dgfs_internal.h"
+
+namespace dgfs {
+
+static constexpr double kPi = 3.141592653589793238462643383279502884;
+
+static bool supported_n(int N) {
+  switch (N) {
+    case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: return true;
+    default: return false;
+  }
+}
+
+size_t real_size(const Plan& p) { return p.precision == DGFS_FP32 ? sizeof(float) : sizeof(double); }
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the three-term
+// recurrence of P_n, w = 2 / ((1 - x^2) P_n'(x)^2).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Built-in spherical designs with equal weights 4 pi / M: octahedron (M = 6),
+// icosahedron (M = 12), icosahedron and dodecahedron together (M = 32).
+static bool builtin_design(int M, std::vector<double>& s) {
+  const double g = (1.0 + std::sqrt(5.0)) / 2.0;
+  s.clear();
+  auto push = [&](double a, double b, double c) {
+    const double n = std::sqrt(a * a + b * b + c * c);
+    s.push_back(a / n);
+    s.push_back(b / n);
+    s.push_back(c / n);
+  };
+  auto icosa = [&]() {
+    for (double a : {1.0, -1.0})
+      for (double b : {g, -g}) {
+        push(0.0, a, b);
+        push(a, b, 0.0);
+        push(b, 0.0, a);
+      }
+  };
+  if (M == 6) {
+    for (int d = 0; d < 3; ++d)
+      for (double sg : {1.0, -1.0}) push(d == 0 ? sg : 0.0, d == 1 ? sg : 0.0, d == 2 ? sg : 0.0);
+    return true;
+  }
+  if (M == 12) {
+    icosa();
+    return true;
+  }
+  if (M == 32) {
+    icosa();
+    for (double a : {1.0, -1.0})
+      for (double b : {1.0, -1.0})
+        for (double c : {1.0, -1.0}) push(a, b, c);
+    const double ig = 1.0 / g;
+    for (double a : {ig, -ig})
+      for (double b : {g, -g}) {
+        push(0.0, a, b);
+        push(a, b, 0.0);
+        push(b, 0.0, a);
+      }
+    return true;
+  }
+  return false;
+}
+
+// b_ij of Eq. NVSS
+static double vss_prefactor(double mi, double mj, double omega, double alpha) {
+  const double mu = mi * mj / (mi + mj);
+  return alpha / (std::sqrt(1.0 + mi / mj) * std::pow(mu, omega - 0.5) * std::pow(2.0, 1.0 + alpha) *
+                  std::tgamma(2.5 - omega) * kPi);
+}
+
+static double sinc(double x) { return std::fabs(x) < 1e-300 ? 1.0 : std::sin(x) / x; }
+
+static int centred_mode(int n, int N) { return n < N / 2 ? n : n - N; }
+
+int build_plan(const dgfs_plan_desc* d, Plan& p) {
+  if (!d) return DGFS_ERR_INVALID_ARG;
+  if (!supported_n(d->N)) return DGFS_ERR_UNSUPPORTED_N;
+  if (!(d->L > 0.0) || d->s < 1 || d->s > 8 || !d->mass || !d->omega || !d->alpha) return DGFS_ERR_INVALID_ARG;
+  if (d->N_rho < 1 || d->N_rho > 4096 || d->M < 1 || d->max_batch < 0) return DGFS_ERR_INVALID_ARG;
+  if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32) return DGFS_ERR_INVALID_ARG;
+  if (d->flags != 0u) return DGFS_ERR_UNSUPPORTED;
+  const int s = d->s;
+  p.N = d->N;
+  p.L = d->L;
+  p.s = s;
+  p.N_rho = d->N_rho;
+  p.precision = d->precision;
+  p.flags = d->flags;
+  p.max_batch = d->max_batch;
+  p.mass.assign(d->mass, d->mass + s);
+  p.omega.assign(d->omega, d->omega + s * s);
+  p.alpha.assign(d->alpha, d->alpha + s * s);
+  for (int i = 0; i < s; ++i)
+    if (!(p.mass[i] > 0.0) || !std::isfinite(p.mass[i])) return DGFS_ERR_INVALID_ARG;
+  for (int k = 0; k < s * s; ++k) {
+    if (!(p.omega[k] >= 0.5 && p.omega[k] <= 1.0)) return DGFS_ERR_INVALID_ARG;
+    if (!(p.alpha[k] >= 1.0 && p.alpha[k] <= 2.0)) return DGFS_ERR_INVALID_ARG;
+    if (p.alpha[k] != 1.0) return DGFS_ERR_UNSUPPORTED;  // VSS gain weights: not in this build
+  }
+  p.b.assign(s * s, 0.0);
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j)
+      p.b[i * s + j] = d->b_override ? d->b_override[i * s + j]
+                                     : vss_prefactor(p.mass[i], p.mass[j], p.omega[i * s + j], p.alpha[i * s + j]);
+  // sphere rule
+  p.M = d->M;
+  if (d->sigma) {
+    p.sigma.assign(d->sigma, d->sigma + 3 * d->M);
+    for (int m = 0; m < d->M; ++m) {
+      const double* v = &p.sigma[3 * m];
+      const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      if (!(std::fabs(n - 1.0) < 1e-9)) return DGFS_ERR_INVALID_ARG;
+    }
+  } else if (!builtin_design(d->M, p.sigma)) {
+    return DGFS_ERR_INVALID_ARG;
+  }
+  if (d->w_sigma) p.w_sigma.assign(d->w_sigma, d->w_sigma + d->M);
+  else p.w_sigma.assign(d->M, 4.0 * kPi / d->M);
+  // radial truncation: R = 2S, S the largest support allowed by Eq. domain for every pair
+  if (d->R > 0.0) {
+    p.R = d->R;
+  } else {
+    double S = 1e300;
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) {
+        const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
+        const double den = std::max(4.0 * cj, 2.0) + std::sqrt(1.0 + p.mass[j] / p.mass[i]) + 1.0;
+        S = std::min(S, 2.0 * p.L / den);
+      }
+    p.R = 2.0 * S;
+  }
+  std::vector<double> x, w;
+  gauss_legendre(p.N_rho, x, w);
+  p.rho.resize(p.N_rho);
+  p.w_rho.resize(p.N_rho);
+  for (int q = 0; q < p.N_rho; ++q) {
+    p.rho[q] = 0.5 * p.R * (x[q] + 1.0);
+    p.w_rho[q] = 0.5 * p.R * w[q];
+  }
+
+  // antipodal partner of every direction (equal weights required for the pair reuse)
+  const int M = p.M;
+  std::vector<int> anti(M, -1);
+  bool antipodal = true;
+  for (int m = 0; m < M; ++m) {
+    for (int k = 0; k < M; ++k) {
+      const double* a = &p.sigma[3 * m];
+      const double* c = &p.sigma[3 * k];
+      if (std::fabs(a[0] + c[0]) < 1e-12 && std::fabs(a[1] + c[1]) < 1e-12 && std::fabs(a[2] + c[2]) < 1e-12 &&
+          std::fabs(p.w_sigma[m] - p.w_sigma[k]) <= 1e-14 * std::fabs(p.w_sigma[m])) {
+        anti[m] = k;
+        break;
+      }
+    }
+    if (anti[m] < 0) antipodal = false;
+  }
+  auto positive = [&](int m) {
+    const double* a = &p.sigma[3 * m];
+    for (int dd = 0; dd < 3; ++dd) {
+      if (a[dd] > 1e-12) return true;
+      if (a[dd] < -1e-12) return false;
+    }
+    return true;
+  };
+
+  // tasks: unordered pairs with (i,j)/(j,i) reuse and halved self pairs when the rule is
+  // antipodal; every ordered pair with the full rule otherwise
+  p.tasks.clear();
+  p.groups.clear();
+  p.ent_w.clear();
+  p.ent_sigma.clear();
+  p.max_ent = 0;
+  for (int i = 0; i < s; ++i) {
+    for (int j = antipodal ? i : 0; j < s; ++j) {
+      std::vector<std::pair<int, double>> ent;
+      for (int m = 0; m < M; ++m) {
+        if (antipodal && i == j) {
+          if (positive(m)) ent.push_back({m, 2.0 * p.w_sigma[m]});
+        } else {
+          ent.push_back({m, p.w_sigma[m]});
+        }
+      }
+      std::stable_sort(ent.begin(), ent.end(), [&](const std::pair<int, double>& a, const std::pair<int, double>& c) {
+        return p.sigma[3 * a.first] < p.sigma[3 * c.first] - 1e-12;
+      });
+      TaskDesc tk;
+      tk.i = i;
+      tk.j = j;
+      tk.out0 = i * s + j;
+      tk.out1 = (antipodal && i != j) ? j * s + i : -1;
+      tk.ent_off = int(p.ent_w.size());
+      tk.n_ent = int(ent.size());
+      tk.grp_off = int(p.groups.size());
+      int first = 0;
+      for (int e = 1; e <= int(ent.size()); ++e) {
+        if (e == int(ent.size()) ||
+            std::fabs(p.sigma[3 * ent[e].first] - p.sigma[3 * ent[first].first]) > 1e-12) {
+          p.groups.push_back({first, e - first});
+          first = e;
+        }
+      }
+      tk.n_grp = int(p.groups.size()) - tk.grp_off;
+      for (auto& e : ent) {
+        p.ent_w.push_back(e.second);
+        p.ent_sigma.push_back(e.first);
+      }
+      p.max_ent = std::max(p.max_ent, tk.n_ent);
+      p.tasks.push_back(tk);
+    }
+  }
+  return DGFS_OK;
+}
+
+template <typename V>
+static int upload(const V* host, size_t count, void** dptr, size_t& total) {
+  const size_t bytes = count * sizeof(V);
+  if (cudaMalloc(dptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *dptr = nullptr;
+    return DGFS_ERR_OOM;
+  }
+  if (cudaMemcpy(*dptr, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return DGFS_ERR_CUDA;
+  total += bytes;
+  return DGFS_OK;
+}
+
+int upload_plan(Plan& p) {
+  const int N = p.N, s = p.s, NR = p.N_rho;
+  const size_t N3 = size_t(N) * N * N;
+  const int P = s * s;
+  // |k| on the FFT-ordered grid (x slowest, z fastest)
+  std::vector<double> kabs(N3);
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b)
+      for (int c = 0; c < N; ++c) {
+        const double kx = centred_mode(a, N), ky = centred_mode(b, N), kz = centred_mode(c, N);
+        kabs[(size_t(a) * N + b) * N + c] = std::sqrt(kx * kx + ky * ky + kz * kz);
+      }
+  // gain weights w_rho F^(ij)(k, rho) / N^3 with F = 4 pi b rho^(4-2 omega) sinc(pi rho c_j |k| / L)
+  // (VHS form of Eq. GG) and loss weights G^(ij)-(k) = 16 pi^2 b sum_q w_q rho_q^(4-2 omega)
+  // sinc(pi rho_q |k| / L) on the same radial rule
+  std::vector<double> Fw(size_t(P) * NR * N3), Gm(size_t(P) * N3, 0.0);
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      const int o = i * s + j;
+      const double b = p.b[o], om = p.omega[o];
+      const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
+      for (int q = 0; q < NR; ++q) {
+        const double rho = p.rho[q];
+        const double pref = p.w_rho[q] * 4.0 * kPi * b * std::pow(rho, 4.0 - 2.0 * om) / double(N3);
+        double* dst = &Fw[(size_t(o) * NR + q) * N3];
+        for (size_t n = 0; n < N3; ++n) dst[n] = pref * sinc(kPi * rho * cj * kabs[n] / p.L);
+        const double gpref = 16.0 * kPi * kPi * b * p.w_rho[q] * std::pow(rho, 4.0 - 2.0 * om);
+        double* g = &Gm[size_t(o) * N3];
+        for (size_t n = 0; n < N3; ++n) g[n] += gpref * sinc(kPi * rho * kabs[n] / p.L);
+      }
+    }
+  // phase factors exp(i pi shift_d k / L) per task, radial node, entry, role, axis
+  const int NT = int(p.tasks.size());
+  const size_t nph = size_t(NT) * NR * p.max_ent * 2 * 3 * N;
+  std::vector<std::complex<double>> ph(nph, std::complex<double>(0.0, 0.0));
+  for (int t = 0; t < NT; ++t) {
+    const TaskDesc& tk = p.tasks[t];
+    const double mi = p.mass[tk.i], mj = p.mass[tk.j];
+    const double ci = mi / (mi + mj), cj = mj / (mi + mj);
+    for (int q = 0; q < NR; ++q)
+      for (int e = 0; e < tk.n_ent; ++e) {
+        const double* sg = &p.sigma[3 * p.ent_sigma[tk.ent_off + e]];
+        for (int role = 0; role < 2; ++role) {
+          const double c = role == 0 ? p.rho[q] * cj : -p.rho[q] * ci;
+          for (int ax = 0; ax < 3; ++ax) {
+            const double sh = c * sg[ax];
+            std::complex<double>* dst = &ph[((((size_t(t) * NR + q) * p.max_ent + e) * 2 + role) * 3 + ax) * N];
+            for (int n = 0; n < N; ++n) {
+              const double arg = kPi * sh * centred_mode(n, N) / p.L;
+              dst[n] = std::complex<double>(std::cos(arg), std::sin(arg));
+            }
+          }
+        }
+      }
+  }
+  size_t total = 0;
+  int rc;
+  if ((rc = upload(Fw.data(), Fw.size(), (void**)&p.d_Fw, total))) return rc;
+  if ((rc = upload(Gm.data(), Gm.size(), (void**)&p.d_Gm, total))) return rc;
+  if ((rc = upload(p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
+  if ((rc = upload(p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
+  if ((rc = upload(p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
+  if (p.precision == DGFS_FP32) {
+    std::vector<float> phf(2 * nph);
+    for (size_t n = 0; n < nph; ++n) {
+      phf[2 * n] = float(ph[n].real());
+      phf[2 * n + 1] = float(ph[n].imag());
+    }
+    if ((rc = upload(phf.data(), phf.size(), &p.d_phase, total))) return rc;
+  } else {
+    std::vector<double> phd(2 * nph);
+    for (size_t n = 0; n < nph; ++n) {
+      phd[2 * n] = ph[n].real();
+      phd[2 * n + 1] = ph[n].imag();
+    }
+    if ((rc = upload(phd.data(), phd.size(), &p.d_phase, total))) return rc;
+  }
+  p.table_bytes = total;
+  if (cudaMalloc(&p.d_scratch, p.scratch_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p.d_scratch = nullptr;
+    return DGFS_ERR_OOM;
+  }
+  return DGFS_OK;
+}
+
+void free_plan(Plan& p) {
+  void* ptrs[] = {p.d_Fw, p.d_Gm, p.d_ent_w, p.d_phase, p.d_tasks, p.d_groups, p.d_scratch, p.d_stage_f, p.d_stage_Q};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p.d_Fw = p.d_Gm = p.d_ent_w = nullptr;
+  p.d_phase = p.d_scratch = p.d_stage_f = p.d_stage_Q = nullptr;
+  p.d_tasks = nullptr;
+  p.d_groups = nullptr;
+}
+
+}  // namespace dgfs

@@ -1,0 +1,239 @@
+"""ctypes binding of libdgfs.so: argument marshalling only.
+
+The functions mirror the C ABI of ``include/dgfs.h`` one to one (same names, same
+arguments, pointers passed as integers).  ``Plan`` is a convenience holder that builds the
+descriptor, owns the handle and accepts torch tensors (their ``data_ptr()``) for device
+memory and ``torch.cuda.Stream`` objects for streams.  Every evaluation runs in the CUDA
+library; there is no other implementation behind this module, and a missing library is an
+error.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdgfs.so")
+
+DGFS_OK = 0
+DGFS_ERR_INVALID_ARG = -1
+DGFS_ERR_UNSUPPORTED_N = -2
+DGFS_ERR_OOM = -3
+DGFS_ERR_BUDGET = -4
+DGFS_ERR_CUDA = -5
+DGFS_ERR_DEVICE_TIMEOUT = -6
+DGFS_ERR_UNSUPPORTED = -7
+DGFS_FP64 = 0
+DGFS_FP32 = 1
+
+EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
+           "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
+           "dgfs_plan_launches", "dgfs_strerror")
+
+_dptr = ctypes.POINTER(ctypes.c_double)
+
+
+class dgfs_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("s", ctypes.c_int),
+                ("mass", _dptr), ("omega", _dptr), ("alpha", _dptr), ("b_override", _dptr),
+                ("M", ctypes.c_int), ("sigma", _dptr), ("w_sigma", _dptr),
+                ("N_rho", ctypes.c_int), ("R", ctypes.c_double), ("precision", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("max_batch", ctypes.c_int)]
+
+
+class DgfsError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s failed: %s (%d)" % (where, dgfs_strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libdgfs.so (built by ``paper_1903_03056_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdgfs.so has not been built (python -m paper_1903_03056_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci, cs = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.dgfs_create_plan.argtypes = [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(vp)]
+    lib.dgfs_destroy_plan.argtypes = [vp]
+    lib.dgfs_eval_collision.argtypes = [vp, vp, vp, ci, vp]
+    lib.dgfs_eval_collision_host.argtypes = [vp, vp, vp, ci, vp]
+    lib.dgfs_plan_bytes.argtypes = [vp, ci, ctypes.POINTER(cs), ctypes.POINTER(cs)]
+    lib.dgfs_plan_radius.argtypes = [vp, _dptr]
+    lib.dgfs_plan_launches.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.dgfs_strerror.argtypes = [ci]
+    lib.dgfs_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "dgfs_strerror":
+            getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != DGFS_OK:
+        raise DgfsError(code, where)
+
+
+# ---- one-to-one wrappers of the C ABI -------------------------------------------------------
+
+def dgfs_create_plan(desc):
+    h = ctypes.c_void_p()
+    code = load().dgfs_create_plan(ctypes.byref(desc), ctypes.byref(h))
+    return code, h.value
+
+
+def dgfs_destroy_plan(plan):
+    return load().dgfs_destroy_plan(plan)
+
+
+def dgfs_eval_collision(plan, f_dev, Q_dev, batch, stream):
+    return load().dgfs_eval_collision(plan, f_dev, Q_dev, batch, stream)
+
+
+def dgfs_eval_collision_host(plan, f_host, Q_host, batch, stream):
+    return load().dgfs_eval_collision_host(plan, f_host, Q_host, batch, stream)
+
+
+def dgfs_plan_bytes(plan, batch):
+    t, w = ctypes.c_size_t(), ctypes.c_size_t()
+    code = load().dgfs_plan_bytes(plan, batch, ctypes.byref(t), ctypes.byref(w))
+    return code, t.value, w.value
+
+
+def dgfs_plan_radius(plan):
+    r = ctypes.c_double()
+    code = load().dgfs_plan_radius(plan, ctypes.byref(r))
+    return code, r.value
+
+
+def dgfs_plan_launches(plan):
+    n = ctypes.c_int()
+    code = load().dgfs_plan_launches(plan, ctypes.byref(n))
+    return code, n.value
+
+
+def dgfs_strerror(code):
+    return load().dgfs_strerror(code).decode()
+
+
+# ---- convenience holder -----------------------------------------------------------------------
+
+def _arr(x, n):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (n,)).copy())
+    return a, a.ctypes.data_as(_dptr)
+
+
+def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision="fp32",
+              b_override=None, sigma=None, w_sigma=None, max_batch=0):
+    """Build a dgfs_plan_desc; returns (desc, keepalive) -- keep the second alive until the
+    plan is created."""
+    s = len(masses)
+    keep = []
+    mass, pm = _arr(masses, s)
+    om, po = _arr(np.asarray(omega, dtype=np.float64).reshape(-1) if np.ndim(omega) else omega, s * s)
+    al, pa = _arr(np.asarray(alpha, dtype=np.float64).reshape(-1) if np.ndim(alpha) else alpha, s * s)
+    keep += [mass, om, al]
+    d = dgfs_plan_desc()
+    d.N, d.L, d.s = int(N), float(L), s
+    d.mass, d.omega, d.alpha = pm, po, pa
+    if b_override is not None:
+        bo, pb = _arr(np.asarray(b_override, dtype=np.float64).reshape(-1), s * s)
+        keep.append(bo)
+        d.b_override = pb
+    if sigma is not None:
+        sg = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(-1))
+        keep.append(sg)
+        d.sigma = sg.ctypes.data_as(_dptr)
+        M = sg.size // 3
+        if w_sigma is not None:
+            ws, pw = _arr(w_sigma, M)
+            keep.append(ws)
+            d.w_sigma = pw
+    d.M = int(M)
+    d.N_rho = int(N if N_rho is None else N_rho)
+    d.R = float(R)
+    d.precision = DGFS_FP32 if precision in ("fp32", DGFS_FP32) else DGFS_FP64
+    d.flags = 0
+    d.max_batch = int(max_batch)
+    return d, keep
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Plan:
+    """Owns one dgfs plan.  ``precision`` is "fp32" or "fp64"."""
+
+    def __init__(self, N, L, masses, omega, **kw):
+        desc, keep = make_desc(N, L, masses, omega, **kw)
+        code, h = dgfs_create_plan(desc)
+        del keep
+        _check(code, "dgfs_create_plan")
+        self.handle = h
+        self.N, self.L, self.s = int(N), float(L), len(masses)
+        self.precision = kw.get("precision", "fp32")
+        self.max_batch = int(kw.get("max_batch", 0))
+
+    @property
+    def dtype_name(self):
+        return "float32" if self.precision in ("fp32", DGFS_FP32) else "float64"
+
+    def radius(self):
+        code, r = dgfs_plan_radius(self.handle)
+        _check(code, "dgfs_plan_radius")
+        return r
+
+    def launches(self):
+        code, n = dgfs_plan_launches(self.handle)
+        _check(code, "dgfs_plan_launches")
+        return n
+
+    def bytes(self, batch=0):
+        code, t, w = dgfs_plan_bytes(self.handle, batch)
+        _check(code, "dgfs_plan_bytes")
+        return t, w
+
+    def eval_ptr(self, f_dev, Q_dev, batch, stream=None):
+        _check(dgfs_eval_collision(self.handle, f_dev, Q_dev, int(batch), _stream_handle(stream)),
+               "dgfs_eval_collision")
+
+    def eval(self, f, Q=None, stream=None):
+        """f: CUDA tensor [B, s, N, N, N] of the plan's dtype; returns Q [B, s, s, N, N, N]."""
+        import torch
+        assert f.is_cuda and f.is_contiguous() and str(f.dtype).endswith(self.dtype_name)
+        B = f.shape[0]
+        if Q is None:
+            Q = torch.empty((B, self.s, self.s) + tuple(f.shape[2:]), dtype=f.dtype, device=f.device)
+        self.eval_ptr(f.data_ptr(), Q.data_ptr(), B, stream)
+        return Q
+
+    def eval_host(self, f_host, Q_host, stream=None):
+        """Host arrays or tensors (contiguous, plan dtype); copies in, evaluates, copies out."""
+        fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data
+        qp = Q_host.data_ptr() if hasattr(Q_host, "data_ptr") else Q_host.ctypes.data
+        _check(dgfs_eval_collision_host(self.handle, fp, qp, int(f_host.shape[0]),
+                                        _stream_handle(stream)), "dgfs_eval_collision_host")
+        return Q_host
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dgfs_destroy_plan(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,50 @@
+"""Evaluate one synthetic workload a few times (for profiling a single kernel launch).
+
+    python -m paper_1903_03056_gb300.run_case --workload dg_batch_n32 --batch 288 \
+        --precision fp32 --repeat 3
+
+Prints one JSON line with the mean time per evaluation measured with CUDA events.
+"""
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="dg_batch_n32")
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args()
+
+    import torch
+
+    from paper_1903_03056_gb300 import build, dgfs, synth
+
+    build.build()
+    w = synth.WORKLOADS[a.workload]
+    B = a.batch or w.batch
+    f = synth.batch_distribution(w, nodes=range(B))
+    dt = torch.float32 if a.precision == "fp32" else torch.float64
+    fd = torch.from_numpy(f).to(device="cuda", dtype=dt)
+    Q = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=dt, device="cuda")
+    plan = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho,
+                     precision=a.precision)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(a.repeat):
+        plan.eval_ptr(fd.data_ptr(), Q.data_ptr(), B, st)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / a.repeat
+    print(json.dumps({"workload": w.name, "batch": B, "precision": a.precision, "ms": ms,
+                      "evals_per_s": B / (ms * 1e-3), "finite": bool(torch.isfinite(Q).all())}))
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,58 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and the
+oracle on the same seeded inputs."""
+
+import numpy as np
+
+from oracle import fast_spectral as fs
+from paper_1903_03056_gb300 import dgfs
+
+# mixed-precision bound of the FP32 path relative to max |Q| (the stated target) and the
+# FP64 path's bound against the FP64 oracle
+TOL_FP32 = 1e-5
+TOL_FP64 = 1e-11
+
+
+def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", sigma=None,
+                  w_sigma=None, b_override=None, R=0.0):
+    """f: numpy [B, s, N, N, N] float64 -> Q numpy [B, s, s, N, N, N] from libdgfs."""
+    import torch
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plan = dgfs.Plan(N, L, masses, omega, M=M, N_rho=N_rho, precision=precision, sigma=sigma,
+                     w_sigma=w_sigma, b_override=b_override, R=R)
+    fd = torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=dt)
+    Q = plan.eval(fd)
+    torch.cuda.synchronize()
+    assert plan.launches() == 1
+    out = Q.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+def oracle_collision(f, *, N, L, masses, omega, M=12, N_rho=8, sigma=None, w_sigma=None,
+                     b_override=None, R=None):
+    prob = fs.make_problem(N, L, masses, omega=omega, M=M, N_rho=N_rho, sigma=sigma,
+                           w_sigma=w_sigma, b_override=b_override, R=R)
+    return np.stack([fs.collision(fb, prob)[0] for fb in f])
+
+
+def max_rel_error(Q_gpu, Q_ref, per="pair"):
+    """Largest max|Q_gpu - Q_ref| / scale over nodes and pairs.
+
+    per="pair": scale = max|Q_ref| of the same node and pair (the FP64 bar);
+    per="node": scale = max|Q_ref| over all s^2 operators of the node (the FP32 bar: a pair
+    whose gain and loss nearly cancel keeps the absolute FP32 error of the larger terms).
+    """
+    err = 0.0
+    for b in range(Q_ref.shape[0]):
+        node_scale = np.max(np.abs(Q_ref[b]))
+        for i in range(Q_ref.shape[1]):
+            for j in range(Q_ref.shape[2]):
+                scale = np.max(np.abs(Q_ref[b, i, j])) if per == "pair" else node_scale
+                err = max(err, np.max(np.abs(Q_gpu[b, i, j] - Q_ref[b, i, j])) / scale)
+    return err
+
+
+def check(Q_gpu, Q_ref, precision):
+    if precision == "fp64":
+        return max_rel_error(Q_gpu, Q_ref, "pair") < TOL_FP64
+    return max_rel_error(Q_gpu, Q_ref, "node") < TOL_FP32

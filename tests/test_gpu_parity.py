@@ -1,0 +1,140 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element on
+the same seeded inputs.  Bars: FP64 path <= 1e-11 max|Q| per node and pair; FP32 path
+<= 1e-5 of max|Q| over the node's s^2 operators (the mixed-precision target)."""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import check, gpu_collision, oracle_collision
+from oracle import fast_spectral as fs, krook_wu
+from paper_1903_03056_gb300 import build, dgfs, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+    dgfs.load()
+
+
+def _inputs(N, L, masses, B, seed, noise=0.0):
+    w = synth.Workload("test", B, N, L, tuple(masses), 0.5, 1.0, 6, 4, "bimaxwellian", noise, seed)
+    return synth.batch_distribution(w)
+
+
+CASES = {
+    # name: (N, L, masses, omega, M, N_rho, B)
+    "single_node_n16": (16, 6.0, (1.0, 2.0), 0.5, 6, 8, 1),
+    "radix3_n24_batch3": (24, 6.0, (1.0, 4.0), 0.5, 12, 4, 3),
+    "three_species_n12": (12, 5.0, (1.0, 1.5, 2.6), 0.74, 12, 4, 2),
+    "n32_single": (32, 7.0, (1.0, 2.1), 0.81, 6, 4, 1),
+    "n8_batch5": (8, 4.0, (1.0, 3.0), 0.6, 6, 3, 5),
+    "n6_three_species": (6, 4.0, (1.0, 2.0, 4.0), 0.9, 6, 2, 2),
+    "n4_single_species": (4, 3.0, (1.0,), 0.7, 12, 2, 3),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_parity_with_oracle(name, precision):
+    N, L, masses, omega, M, N_rho, B = CASES[name]
+    f = _inputs(N, L, masses, B, seed=100 + N)
+    kw = dict(N=N, L=L, masses=masses, omega=omega, M=M, N_rho=N_rho)
+    Q = gpu_collision(f, precision=precision, **kw)
+    ref = oracle_collision(f, **kw)
+    assert check(Q, ref, precision)
+
+
+def test_parity_n48_fp32():
+    kw = dict(N=48, L=8.0, masses=(1.0, 2.6), omega=0.74, M=6, N_rho=2)
+    f = _inputs(48, 8.0, (1.0, 2.6), 1, seed=148)
+    Q = gpu_collision(f, precision="fp32", **kw)
+    assert check(Q, oracle_collision(f, **kw), "fp32")
+
+
+def test_parity_n48_fp64():
+    kw = dict(N=48, L=8.0, masses=(1.0, 2.6), omega=0.74, M=6, N_rho=1)
+    f = _inputs(48, 8.0, (1.0, 2.6), 1, seed=248)
+    Q = gpu_collision(f, precision="fp64", **kw)
+    assert check(Q, oracle_collision(f, **kw), "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_parity_non_antipodal_rule(precision):
+    """A sphere rule that is not closed under sigma -> -sigma: every ordered pair is its own
+    task (no (i,j)/(j,i) reuse, no halving)."""
+    rng = np.random.default_rng(5)
+    sigma = rng.normal(size=(7, 3))
+    sigma /= np.linalg.norm(sigma, axis=1, keepdims=True)
+    w = rng.uniform(0.5, 1.5, size=7)
+    w *= 4 * np.pi / w.sum()
+    kw = dict(N=8, L=4.0, masses=(1.0, 2.0), omega=0.7, N_rho=3, sigma=sigma, w_sigma=w)
+    f = _inputs(8, 4.0, (1.0, 2.0), 2, seed=77)
+    Q = gpu_collision(f, precision=precision, **kw)
+    ref = oracle_collision(f, **kw)
+    assert check(Q, ref, precision)
+
+
+def test_plan_radius_matches_domain_rule():
+    plan = dgfs.Plan(32, 7.0, [1.0, 2.1], 0.81, M=12, N_rho=16, precision="fp32")
+    prob = fs.make_problem(32, 7.0, [1.0, 2.1], omega=0.81, M=12, N_rho=16)
+    assert abs(plan.radius() - prob.R) < 1e-14 * prob.R
+    plan.close()
+
+
+def test_krook_wu_exact_solution_on_gpu():
+    """Sum_j Q_ij from the FP64 GPU path against the exact d_t f of the Krook-Wu solution:
+    the error equals the oracle's (and Table 1's magnitude, N=32, N_rho=16, m1/m2=4)."""
+    N, L, ratio = 32, 12.0, 4.0
+    kw_sol = krook_wu.KrookWu(ratio, 1.0)
+    v = fs.velocity_grid(N, L)
+    vx, vy, vz = np.meshgrid(v, v, v, indexing="ij")
+    v2 = vx * vx + vy * vy + vz * vz
+    f = np.stack([kw_sol.f(0, 4.0, v2), kw_sol.f(1, 4.0, v2)])[None]
+    Q = gpu_collision(f, N=N, L=L, masses=(ratio, 1.0), omega=1.0, M=6, N_rho=16,
+                      precision="fp64", b_override=kw_sol.kernel_prefactors())
+    err = [np.max(np.abs(Q[0, i].sum(axis=0) - kw_sol.df(i, 4.0, v2))) for i in range(2)]
+    paper = (8.018e-03, 9.020e-04)
+    for e, p in zip(err, paper):
+        assert 0.5 < e / p < 2.0
+
+
+def test_batch_zero_and_bad_pointers():
+    import torch
+    plan = dgfs.Plan(8, 4.0, [1.0, 2.0], 0.5, M=6, N_rho=2, precision="fp32")
+    assert dgfs.dgfs_eval_collision(plan.handle, None, None, 0, None) == dgfs.DGFS_OK
+    buf = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    assert dgfs.dgfs_eval_collision(plan.handle, buf.data_ptr() + 4, buf.data_ptr(), 1, None) \
+        == dgfs.DGFS_ERR_INVALID_ARG
+    assert dgfs.dgfs_eval_collision(plan.handle, buf.data_ptr(), buf.data_ptr(), -1, None) \
+        == dgfs.DGFS_ERR_INVALID_ARG
+    plan.close()
+
+
+def test_deterministic_repeat():
+    import torch
+    f = _inputs(16, 6.0, (1.0, 2.0), 3, seed=9)
+    plan = dgfs.Plan(16, 6.0, [1.0, 2.0], 0.5, M=12, N_rho=4, precision="fp32")
+    fd = torch.from_numpy(f).float().cuda()
+    a = plan.eval(fd).clone()
+    b = plan.eval(fd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_host_buffer_entry_point(precision):
+    import torch
+    f = _inputs(12, 5.0, (1.0, 2.0), 4, seed=31)
+    dt = np.float32 if precision == "fp32" else np.float64
+    plan = dgfs.Plan(12, 5.0, [1.0, 2.0], 0.6, M=6, N_rho=3, precision=precision, max_batch=4)
+    fh = np.ascontiguousarray(f.astype(dt))
+    Qh = np.zeros((4, 2, 2, 12, 12, 12), dtype=dt)
+    plan.eval_host(fh, Qh)
+    Qd = plan.eval(torch.from_numpy(fh).cuda()).cpu().numpy()
+    assert np.array_equal(Qh, Qd)
+    with pytest.raises(dgfs.DgfsError):
+        plan.eval_host(np.zeros((5, 2, 12, 12, 12), dtype=dt), np.zeros((5, 2, 2, 12, 12, 12), dtype=dt))
+    plan.close()

@@ -107,6 +107,31 @@ int dgfs_plan_launches(dgfs_plan plan, int* launches);
 /* Static text naming a return code. */
 const char* dgfs_strerror(int code);
 
+/* The evaluation of dgfs_eval_collision for callers that cannot allocate device memory
+ * (no counterpart in the paper; it exists for embedding).  A solver plugin whose host
+ * application owns every device allocation, or code that may not call cudaMalloc after
+ * start-up, cannot create a plan, because dgfs_create_plan allocates tables and a workspace.
+ * This call takes the plan description itself, needs no plan, and allocates nothing: the
+ * quadrature and kernel constants travel in the kernel's parameter block, the gain and loss
+ * weights and the phase factors are computed inside the kernel, and the workspace is a
+ * static device array of 14.7 MB (64 work slots of 7 * 16^3 complex floats) that every GPU
+ * loading the library holds until the process exits.
+ *
+ * desc, f_dev, Q_dev, batch and stream mean what they mean for dgfs_create_plan and
+ * dgfs_eval_collision (f and Q on the current device, float, 16-byte aligned);
+ * desc->max_batch is ignored.  Limits: desc->precision == DGFS_FP32, N in {8, 12, 16}
+ * (else DGFS_ERR_UNSUPPORTED_N), s <= 3, M <= 12, N_rho <= 16, alpha == 1 (else
+ * DGFS_ERR_UNSUPPORTED); these are checked before any work.  Batches of any size run on at
+ * most 64 CTAs.
+ * The first call on a device looks up the workspace's device address and sets the kernels'
+ * shared-memory limits (cudaGetSymbolAddress, cudaFuncSetAttribute); make that first call
+ * before any stream capture.  Every call on a device shares the one workspace: calls whose
+ * kernels overlap on the GPU (different streams, no ordering between them) race and give
+ * wrong results; calls ordered on one stream do not.  Results equal dgfs_eval_collision's
+ * within FP32 rounding. */
+int dgfs_eval_collision_noalloc(const dgfs_plan_desc* desc, const void* f_dev, void* Q_dev,
+                                int batch, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

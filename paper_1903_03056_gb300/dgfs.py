@@ -29,7 +29,7 @@ DGFS_FP32 = 1
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
-           "dgfs_plan_launches", "dgfs_strerror")
+           "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -67,6 +67,7 @@ def load():
     lib.dgfs_plan_bytes.argtypes = [vp, ci, ctypes.POINTER(cs), ctypes.POINTER(cs)]
     lib.dgfs_plan_radius.argtypes = [vp, _dptr]
     lib.dgfs_plan_launches.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.dgfs_eval_collision_noalloc.argtypes = [ctypes.POINTER(dgfs_plan_desc), vp, vp, ci, vp]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -121,6 +122,10 @@ def dgfs_plan_launches(plan):
 
 def dgfs_strerror(code):
     return load().dgfs_strerror(code).decode()
+
+
+def dgfs_eval_collision_noalloc(desc, f_dev, Q_dev, batch, stream):
+    return load().dgfs_eval_collision_noalloc(ctypes.byref(desc), f_dev, Q_dev, batch, stream)
 
 
 # ---- convenience holder -----------------------------------------------------------------------

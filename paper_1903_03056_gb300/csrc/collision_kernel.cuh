@@ -68,6 +68,9 @@ struct Geo {
   static_assert(PLANES % GP == 0, "planes must split evenly over plane groups");
   static_assert(N2 % CL == 0, "pencils must split evenly over the cluster");
   static constexpr size_t SMEM = size_t(GP) * NBUF * N * PITCH * sizeof(C<T>);
+  // workspace volumes per cluster: f_hat_i, f_hat_j, two double-buffered pairs of shifted
+  // volumes, P, and the two gain accumulators
+  static constexpr int SLOT = 9;
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -90,7 +93,18 @@ __device__ __forceinline__ void cluster_sync() {
 template <typename T> __device__ __forceinline__ C<T> ld2(const C<T>* p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __stcg(p, v); }
 
-template <typename T> __device__ __forceinline__ C<T> ldphase(const C<T>* p) { return __ldg(p); }
+
+// Barrier of one plane group.  A group of N threads that divides a warp lives inside one warp
+// and synchronises only that warp, so the plane groups of a CTA run independently; other
+// sizes fall back to the CTA barrier (every group then runs the same control flow).
+template <int N>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (N <= 32 && 32 % N == 0) {
+    __syncwarp();
+  } else {
+    __syncthreads();
+  }
+}
 
 // transpose a plane held as column t (x[r] = V[r][t]) into row t (x[c] = V[t][c]) and back
 template <typename T, int N>
@@ -98,20 +112,20 @@ __device__ __forceinline__ void cols_to_rows(C<T> (&x)[N], C<T>* tb, int t) {
   constexpr int P = N + 1;
 #pragma unroll
   for (int r = 0; r < N; ++r) tb[r * P + t] = x[r];
-  __syncthreads();
+  group_sync<N>();
 #pragma unroll
   for (int c = 0; c < N; ++c) x[c] = tb[t * P + c];
-  __syncthreads();
+  group_sync<N>();
 }
 template <typename T, int N>
 __device__ __forceinline__ void rows_to_cols(C<T> (&x)[N], C<T>* tb, int t) {
   constexpr int P = N + 1;
 #pragma unroll
   for (int c = 0; c < N; ++c) tb[t * P + c] = x[c];
-  __syncthreads();
+  group_sync<N>();
 #pragma unroll
   for (int r = 0; r < N; ++r) x[r] = tb[r * P + t];
-  __syncthreads();
+  group_sync<N>();
 }
 
 template <typename T, int N>
@@ -135,18 +149,23 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
   CT* tb = reinterpret_cast<CT*>(smem_raw) + size_t(grp) * G::NBUF * N * PITCH;
   CT* ab = tb + N * PITCH;
   CT* pb = ab + N * PITCH;  // used only when !PREG
+  // phase block of the current (task, rho): [entry][role][axis][N], when staged in smem
+  CT* const phs = reinterpret_cast<CT*>(smem_raw) + size_t(GP) * G::NBUF * N * PITCH;
+  const bool ph_smem = p.phase_smem != 0;
 
   const int rank = CL == 1 ? 0 : int(cluster_rank());
   const int cid = blockIdx.x / CL;
   const int n_clusters = gridDim.x / CL;
-  CT* scr = reinterpret_cast<CT*>(p.scratch) + size_t(cid) * 7 * N3;
+  CT* scr = reinterpret_cast<CT*>(p.scratch) + size_t(cid) * G::SLOT * N3;
   CT* const FI = scr;
   CT* const FJ = scr + N3;
-  CT* const HA = scr + 2 * N3;
-  CT* const HB = scr + 3 * N3;
-  CT* const PV = scr + 4 * N3;
-  CT* const QA = scr + 5 * N3;
-  CT* const QB = scr + 6 * N3;
+  CT* const HA0 = scr + 2 * N3;
+  CT* const HB0 = scr + 3 * N3;
+  CT* const HA1 = scr + 4 * N3;
+  CT* const HB1 = scr + 5 * N3;
+  CT* const PV = scr + 6 * N3;
+  CT* const QA = scr + 7 * N3;
+  CT* const QB = scr + 8 * N3;
   const int plane0 = rank * G::PLANES;
   const int pencil0 = rank * G::PENCILS;
   const T inv_n3 = T(1) / T(N3);
@@ -191,89 +210,106 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
     const CT* FJs = nspec == 2 ? FJ : FI;
 
     // ---- gain: radial nodes, sigma_x groups, entries ----------------------------------------
+    // Phase k runs step A of group k (into buffer k&1) and step B of group k-1 (from buffer
+    // (k-1)&1); one cluster barrier per phase, n_grp + 1 phases per radial node.
     for (int q = 0; q < p.n_rho; ++q) {
-      for (int gi = 0; gi < tk.n_grp; ++gi) {
-        const GroupDesc gd = p.groups[tk.grp_off + gi];
-        // step A: x-pencils with the group's shared x phase
-        for (int u = tid; u < 2 * G::PENCILS; u += NT) {
-          const int role = u / G::PENCILS;
-          const int pp = pencil0 + u % G::PENCILS;
-          const CT* src = role == 0 ? FI : FJs;
-          const CT* ph = phase_ptr<T, N>(p, task, q, gd.first, role, 0);
-          CT v[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) v[n] = cmul<T>(ld2<T>(src + n * N2 + pp), ldphase<T>(ph + n));
-          fft_line<T, N, +1>(v);
-          CT* dst = role == 0 ? HA : HB;
-#pragma unroll
-          for (int n = 0; n < N; ++n) st2<T>(dst + n * N2 + pp, v[n]);
-        }
-        cluster_sync<CL>();
-        // step B: (y, z) planes
-        const bool last = gi == tk.n_grp - 1;
-        for (int xl = grp; xl < G::PLANES; xl += GP) {
-          const int x = plane0 + xl;
-          CT P[G::PREG ? N : 1];
-          if constexpr (G::PREG) {
-#pragma unroll
-            for (int c = 0; c < N; ++c) P[c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
-          } else {
-#pragma unroll
-            for (int c = 0; c < N; ++c) pb[t * PITCH + c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
-          }
-          for (int e = gd.first; e < gd.first + gd.count; ++e) {
-            const T w = T(p.ent_w[tk.ent_off + e]);
+      const CT* const phq = phase_ptr<T, N>(p, task, q, 0, 0, 0);
+      if (ph_smem) {
+        for (int u = tid; u < tk.n_ent * 6 * N; u += NT) phs[u] = __ldg(phq + u);
+        __syncthreads();
+      }
+      const CT* const phb = ph_smem ? phs : phq;
+      for (int k = 0; k <= tk.n_grp; ++k) {
+        if (k < tk.n_grp) {
+          const GroupDesc gd = p.groups[tk.grp_off + k];
+          CT* const dA = (k & 1) ? HA1 : HA0;
+          CT* const dB = (k & 1) ? HB1 : HB0;
+          // step A: x-pencils with the group's shared x phase
+          for (int u = tid; u < 2 * G::PENCILS; u += NT) {
+            const int role = u / G::PENCILS;
+            const int pp = pencil0 + u % G::PENCILS;
+            const CT* src = role == 0 ? FI : FJs;
+            const CT* ph = phb + ((gd.first * 2 + role) * 3 + 0) * N;
             CT v[N];
-            for (int role = 0; role < 2; ++role) {
-              const CT* vol = (role == 0 ? HA : HB) + size_t(x) * N2;
-              const CT* phy = phase_ptr<T, N>(p, task, q, e, role, 1);
-              const CT* phz = phase_ptr<T, N>(p, task, q, e, role, 2);
 #pragma unroll
-              for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), ldphase<T>(phy + r));
-              fft_line<T, N, +1>(v);
-              cols_to_rows<T, N>(v, tb, t);
+            for (int n = 0; n < N; ++n) v[n] = cmul<T>(ld2<T>(src + n * N2 + pp), ph[n]);
+            fft_line<T, N, +1>(v);
+            CT* dst = role == 0 ? dA : dB;
 #pragma unroll
-              for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], ldphase<T>(phz + c));
-              fft_line<T, N, +1>(v);
-              if (role == 0) {
-#pragma unroll
-                for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
-              }
-            }
+            for (int n = 0; n < N; ++n) st2<T>(dst + n * N2 + pp, v[n]);
+          }
+        }
+        if (k > 0) {
+          const int gi = k - 1;
+          const GroupDesc gd = p.groups[tk.grp_off + gi];
+          const CT* const sA = (gi & 1) ? HA1 : HA0;
+          const CT* const sB = (gi & 1) ? HB1 : HB0;
+          // step B: (y, z) planes
+          const bool last = gi == tk.n_grp - 1;
+          for (int xl = grp; xl < G::PLANES; xl += GP) {
+            const int x = plane0 + xl;
+            CT P[G::PREG ? N : 1];
             if constexpr (G::PREG) {
 #pragma unroll
-              for (int c = 0; c < N; ++c) {
-                const CT a = ab[t * PITCH + c];
-                const CT ab_ = cmul<T>(a, v[c]);
-                P[c] = mk<T>(P[c].x + w * ab_.x, P[c].y + w * ab_.y);
+              for (int c = 0; c < N; ++c) P[c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+            } else {
+#pragma unroll
+              for (int c = 0; c < N; ++c) pb[t * PITCH + c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+            }
+            for (int e = gd.first; e < gd.first + gd.count; ++e) {
+              const T w = T(p.ent_w[tk.ent_off + e]);
+              CT v[N];
+              for (int role = 0; role < 2; ++role) {
+                const CT* vol = (role == 0 ? sA : sB) + size_t(x) * N2;
+                const CT* phy = phb + ((e * 2 + role) * 3 + 1) * N;
+                const CT* phz = phb + ((e * 2 + role) * 3 + 2) * N;
+#pragma unroll
+                for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
+                fft_line<T, N, +1>(v);
+                cols_to_rows<T, N>(v, tb, t);
+#pragma unroll
+                for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], phz[c]);
+                fft_line<T, N, +1>(v);
+                if (role == 0) {
+#pragma unroll
+                  for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
+                }
               }
+              if constexpr (G::PREG) {
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                  const CT a = ab[t * PITCH + c];
+                  const CT ab_ = cmul<T>(a, v[c]);
+                  P[c] = mk<T>(P[c].x + w * ab_.x, P[c].y + w * ab_.y);
+                }
+              } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                  const CT a = ab[t * PITCH + c];
+                  const CT ab_ = cmul<T>(a, v[c]);
+                  const CT o = pb[t * PITCH + c];
+                  pb[t * PITCH + c] = mk<T>(o.x + w * ab_.x, o.y + w * ab_.y);
+                }
+              }
+            }
+            if (last) {
+              CT v[N];
+#pragma unroll
+              for (int c = 0; c < N; ++c) {
+                if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
+              }
+              fft_line<T, N, -1>(v);
+              rows_to_cols<T, N>(v, tb, t);
+              fft_line<T, N, -1>(v);
+#pragma unroll
+              for (int r = 0; r < N; ++r) st2<T>(PV + x * N2 + r * N + t, v[r]);
             } else {
 #pragma unroll
               for (int c = 0; c < N; ++c) {
-                const CT a = ab[t * PITCH + c];
-                const CT ab_ = cmul<T>(a, v[c]);
-                const CT o = pb[t * PITCH + c];
-                pb[t * PITCH + c] = mk<T>(o.x + w * ab_.x, o.y + w * ab_.y);
+                CT val;
+                if constexpr (G::PREG) val = P[c]; else val = pb[t * PITCH + c];
+                st2<T>(PV + x * N2 + c * N + t, val);
               }
-            }
-          }
-          if (last) {
-            CT v[N];
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-              if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
-            }
-            fft_line<T, N, -1>(v);
-            rows_to_cols<T, N>(v, tb, t);
-            fft_line<T, N, -1>(v);
-#pragma unroll
-            for (int r = 0; r < N; ++r) st2<T>(PV + x * N2 + r * N + t, v[r]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < N; ++c) {
-              CT val;
-              if constexpr (G::PREG) val = P[c]; else val = pb[t * PITCH + c];
-              st2<T>(PV + x * N2 + c * N + t, val);
             }
           }
         }
@@ -319,12 +355,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
         for (int n = 0; n < N; ++n) v[n] = ld2<T>(acc + n * N2 + pp);
         fft_line<T, N, +1>(v);
 #pragma unroll
-        for (int n = 0; n < N; ++n) st2<T>(HA + n * N2 + pp, v[n]);
+        for (int n = 0; n < N; ++n) st2<T>(HA0 + n * N2 + pp, v[n]);
 #pragma unroll
         for (int n = 0; n < N; ++n) v[n] = scale<T>(ld2<T>(Fj + n * N2 + pp), T(__ldg(Gm + n * N2 + pp)));
         fft_line<T, N, +1>(v);
 #pragma unroll
-        for (int n = 0; n < N; ++n) st2<T>(HB + n * N2 + pp, v[n]);
+        for (int n = 0; n < N; ++n) st2<T>(HB0 + n * N2 + pp, v[n]);
       }
       cluster_sync<CL>();
       T* Qout = reinterpret_cast<T*>(p.Q) + ((size_t(b) * p.s + io) * p.s + jo) * N3;
@@ -334,14 +370,14 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
         CT v[N];
         T gain[N];
 #pragma unroll
-        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA + x * N2 + r * N + t);
+        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA0 + x * N2 + r * N + t);
         fft_line<T, N, +1>(v);
         cols_to_rows<T, N>(v, tb, t);
         fft_line<T, N, +1>(v);
 #pragma unroll
         for (int c = 0; c < N; ++c) gain[c] = v[c].x;
 #pragma unroll
-        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB + x * N2 + r * N + t);
+        for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB0 + x * N2 + r * N + t);
         fft_line<T, N, +1>(v);
         cols_to_rows<T, N>(v, tb, t);
         fft_line<T, N, +1>(v);
@@ -349,10 +385,10 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
         T* rb = reinterpret_cast<T*>(tb);
 #pragma unroll
         for (int c = 0; c < N; ++c) rb[t * PITCH + c] = gain[c] - __ldg(fi + x * N2 + t * N + c) * v[c].x;
-        __syncthreads();
+        group_sync<N>();
 #pragma unroll
         for (int r = 0; r < N; ++r) Qout[x * N2 + r * N + t] = rb[r * PITCH + t];
-        __syncthreads();
+        group_sync<N>();
       }
       cluster_sync<CL>();
     }
@@ -364,7 +400,11 @@ template <typename T, int N>
 int configure_impl(Plan& pl) {
   using G = Geo<T, N>;
   auto kern = collision_kernel<T, N>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(G::SMEM)) != cudaSuccess)
+  // stage the phase block of the current (task, rho) in shared memory when it fits
+  const size_t ph_bytes = size_t(pl.max_ent) * 6 * N * sizeof(C<T>);
+  const bool ph_smem = G::SMEM + ph_bytes <= size_t(200) * 1024;
+  const size_t smem = G::SMEM + (ph_smem ? ph_bytes : 0);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return DGFS_ERR_CUDA;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -374,7 +414,7 @@ int configure_impl(Plan& pl) {
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(G::CL);
   cfg.blockDim = dim3(G::THREADS);
-  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.dynamicSmemBytes = smem;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
@@ -385,9 +425,10 @@ int configure_impl(Plan& pl) {
   pl.shape.cluster = G::CL;
   pl.shape.groups = G::GP;
   pl.shape.threads = G::THREADS;
-  pl.shape.smem = G::SMEM;
+  pl.shape.smem = smem;
+  pl.shape.phase_smem = ph_smem ? 1 : 0;
   pl.shape.clusters = clusters;
-  pl.scratch_bytes = size_t(clusters) * 7 * G::N3 * sizeof(C<T>);
+  pl.scratch_bytes = size_t(clusters) * G::SLOT * G::N3 * sizeof(C<T>);
   return DGFS_OK;
 }
 
@@ -409,6 +450,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.Fw = pl.d_Fw;
   kp.Gm = pl.d_Gm;
   kp.scratch = pl.d_scratch;
+  kp.phase_smem = pl.shape.phase_smem;
   const int items = batch * kp.n_tasks;
   const int clusters = items < pl.shape.clusters ? items : pl.shape.clusters;
   cudaLaunchConfig_t cfg = {};
@@ -419,7 +461,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(clusters * G::CL);
   cfg.blockDim = dim3(G::THREADS);
-  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.dynamicSmemBytes = pl.shape.smem;
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;

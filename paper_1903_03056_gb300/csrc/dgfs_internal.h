@@ -37,7 +37,8 @@ struct KernelParams {
   const void* phase;      // complex: [task][rho][max_ent][role 2][axis 3][N]
   const double* Fw;       // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3
   const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
-  void* scratch;          // complex: [clusters][7][N^3]
+  void* scratch;          // complex: [clusters][9][N^3]
+  int phase_smem;         // 1: the task's phase block of the current rho is staged in smem
 };
 
 struct LaunchShape {
@@ -45,6 +46,7 @@ struct LaunchShape {
   int groups = 1;         // plane groups per CTA
   int threads = 0;        // groups * N
   size_t smem = 0;        // dynamic shared memory per CTA
+  int phase_smem = 0;     // phases staged in shared memory
   int clusters = 0;       // resident clusters (persistent grid)
 };
 

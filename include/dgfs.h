@@ -53,6 +53,11 @@ extern "C" {
 #define DGFS_FP64 0
 #define DGFS_FP32 1
 
+/* plan flags */
+#define DGFS_CONSERVE 1u    /* project each self pair and each stacked cross pair onto the
+                               discrete conservation laws (Eq. consv) with FP64 moment sums */
+#define DGFS_SUM_SPECIES 2u /* return sum_j kappa_ij Q_ij per species (Eq. NMBE right-hand side) */
+
 typedef struct dgfs_plan_s* dgfs_plan; /* opaque, owned by the library */
 
 /* Plan description.  All arrays are host memory, read during dgfs_create_plan only. */
@@ -70,8 +75,10 @@ typedef struct {
   int N_rho;               /* Gauss-Legendre points in rho on [0, R], >= 1 */
   double R;                /* radial truncation; <= 0 selects R = 2S with S from Eq. domain */
   int precision;           /* DGFS_FP64 or DGFS_FP32 */
-  unsigned flags;          /* reserved, must be 0 */
-  int max_batch;           /* largest batch a host-buffer call will pass (>= 0) */
+  unsigned flags;          /* 0 or DGFS_CONSERVE | DGFS_SUM_SPECIES */
+  int max_batch;           /* largest batch of a host-buffer call or of a DGFS_SUM_SPECIES plan */
+  const double* kappa;     /* nullable [s*s]: species-sum weights kappa_ij (e.g. 1/Kn_ij, Eq. Kn);
+                              NULL = 1.  Used with DGFS_SUM_SPECIES only. */
 } dgfs_plan_desc;
 
 /* Build the tables (Gauss-Legendre rule, design, b_ij of Eq. NVSS, R of Eq. domain, gain
@@ -85,7 +92,14 @@ int dgfs_destroy_plan(dgfs_plan plan);
 /* Q = all s^2 collision operators of the batch (Sec. 4), device pointers, stream-ordered.
  * f_dev: [batch][s][N][N][N], Q_dev: [batch][s][s][N][N][N], element type per precision,
  * both 16-byte aligned.  batch >= 0 (0 is a no-op).  Calls on one plan must not overlap
- * in time on the device (the workspace is shared); they do not when issued on one stream. */
+ * in time on the device (the workspace is shared); they do not when issued on one stream.
+ * With DGFS_CONSERVE every self pair Q_ii and every stacked cross pair [Q_ij; Q_ji] is
+ * replaced by its nearest (L2) vector satisfying the discrete laws of Eq. consv: mass of each
+ * operator, and m_i w_ij int v Q_ij + m_j w_ji int v Q_ji = 0 and the same with |v|^2, with
+ * w_ij = 1 / b_ij (the pair weights under which the kernel is symmetric, b_ij kappa = 1/Kn_ij
+ * for Eq. NVSS); the moment sums and the 5x5 / 6x6 solves are FP64 on the device.
+ * With DGFS_SUM_SPECIES Q_dev is [batch][s][N][N][N] and receives sum_j kappa_ij Q_ij; then
+ * batch <= max_batch (else DGFS_ERR_BUDGET), the full operators being staged in the plan. */
 int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batch, void* stream);
 
 /* The same evaluation from host buffers (pinned or pageable): copies f to the device,

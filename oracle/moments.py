@@ -69,3 +69,54 @@ def conservation_residuals(Q, masses, L, kappa=None):
             out["energy"][i, j] = ((mi * a + mj * b) * v2).sum() * dv3
             out["energy_scale"][i, j] = ((mi * np.abs(a) + mj * np.abs(b)) * v2).sum() * dv3
     return out
+
+
+def _constraint_rows(N, L, masses, i, j, w):
+    """Constraint vectors of the conservation laws (Eq. consv) on the grid.
+
+    Self pair (i, i): rows 1, v_x, v_y, v_z, |v|^2 acting on Q_ii (5 x N^3).
+    Cross pair (i, j): acting on the stacked [Q_ij; Q_ji] (6 x 2N^3): mass of each half,
+    m_i w_ij v + m_j w_ji v (3 rows) and m_i w_ij |v|^2 + m_j w_ji |v|^2, where w_ij are the
+    pair weights under which the laws hold (w_ij = 1 / b_ij: the weighted operators share one
+    symmetric kernel).
+    """
+    vx, vy, vz = grid_vectors(N, L)
+    v2 = vx * vx + vy * vy + vz * vz
+    one = np.ones_like(vx)
+    if i == j:
+        return np.stack([one, vx, vy, vz, v2]).reshape(5, -1)
+    zero = np.zeros_like(vx)
+    a, b = masses[i] * w[i, j], masses[j] * w[j, i]
+    top = [one, zero, a * vx, a * vy, a * vz, a * v2]
+    bot = [zero, one, b * vx, b * vy, b * vz, b * v2]
+    return np.concatenate([np.stack(top).reshape(6, -1), np.stack(bot).reshape(6, -1)], axis=1)
+
+
+def conservation_projection(Q, masses, L, b):
+    """Minimal-L2 correction of Q that makes the discrete conservation laws exact:
+    Q <- Q - C^T (C C^T)^-1 C Q for every self pair and every stacked cross pair
+    (the post-processing reading listed in the design doc; the paper's fast method itself is not
+    exactly conservative).  Q[s, s, N, N, N]; returns a corrected copy."""
+    Q = np.array(Q, dtype=np.float64, copy=True)
+    s, N = Q.shape[0], Q.shape[-1]
+    w = 1.0 / np.asarray(b, dtype=np.float64)
+    for i in range(s):
+        for j in range(i, s):
+            C = _constraint_rows(N, L, masses, i, j, w)
+            x = Q[i, i].reshape(-1) if i == j else np.concatenate([Q[i, j].reshape(-1), Q[j, i].reshape(-1)])
+            lam = np.linalg.solve(C @ C.T, C @ x)
+            x = x - C.T @ lam
+            if i == j:
+                Q[i, i] = x.reshape(N, N, N)
+            else:
+                Q[i, j] = x[:N ** 3].reshape(N, N, N)
+                Q[j, i] = x[N ** 3:].reshape(N, N, N)
+    return Q
+
+
+def species_sum(Q, kappa=None):
+    """sum_j kappa_ij Q_ij for every species i (the right-hand side of Eq. NMBE with
+    kappa_ij = 1 / Kn_ij).  Q[s, s, ...] -> [s, ...]."""
+    s = Q.shape[0]
+    kappa = np.ones((s, s)) if kappa is None else np.asarray(kappa, dtype=np.float64)
+    return np.einsum("ij,ij...->i...", kappa, Q)

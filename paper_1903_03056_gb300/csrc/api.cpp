@@ -26,16 +26,33 @@ struct DeviceGuard {
 
 bool aligned16(const void* p) { return (reinterpret_cast<std::uintptr_t>(p) & 15u) == 0; }
 
-int launch(const dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
-  const int rc = p.precision == DGFS_FP32 ? dgfs::launch_f32(p, f, Q, batch, st)
-                                          : dgfs::launch_f64(p, f, Q, batch, st);
+// collision kernel, then (flags) the conservation projection and the species sum;
+// returns the number of kernels enqueued through *launches
+int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+  p.last_launches = 0;
+  const bool sum = (p.flags & DGFS_SUM_SPECIES) != 0u;
+  if (sum && (batch > p.max_batch || !p.d_Qfull)) return DGFS_ERR_BUDGET;
+  void* Qfull = sum ? p.d_Qfull : Q;
+  int rc = p.precision == DGFS_FP32 ? dgfs::launch_f32(p, f, Qfull, batch, st)
+                                    : dgfs::launch_f64(p, f, Qfull, batch, st);
   if (rc != DGFS_OK) return rc;
+  p.last_launches = 1;
+  if (p.flags & DGFS_CONSERVE) {
+    if ((rc = dgfs::launch_conserve(p, Qfull, batch, st)) != DGFS_OK) return rc;
+    p.last_launches += 1;
+  }
+  if (sum) {
+    if ((rc = dgfs::launch_species_sum(p, Qfull, Q, batch, st)) != DGFS_OK) return rc;
+    p.last_launches += 1;
+  }
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return DGFS_ERR_CUDA;
   }
   return DGFS_OK;
 }
+
+size_t output_pairs(const dgfs::Plan& p) { return (p.flags & DGFS_SUM_SPECIES) ? size_t(p.s) : size_t(p.s) * p.s; }
 
 }  // namespace
 
@@ -78,9 +95,7 @@ int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batc
   if (!f_dev || !Q_dev || !aligned16(f_dev) || !aligned16(Q_dev)) return DGFS_ERR_INVALID_ARG;
   DeviceGuard g(plan->plan.device);
   if (!g.ok) return DGFS_ERR_CUDA;
-  const int rc = launch(plan->plan, f_dev, Q_dev, batch, static_cast<cudaStream_t>(stream));
-  plan->plan.last_launches = rc == DGFS_OK ? 1 : 0;
-  return rc;
+  return launch(plan->plan, f_dev, Q_dev, batch, static_cast<cudaStream_t>(stream));
 }
 
 int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, int batch, void* stream) {
@@ -93,10 +108,10 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   if (!g.ok) return DGFS_ERR_CUDA;
   const size_t n3 = size_t(p.N) * p.N * p.N;
   const size_t fb = size_t(batch) * p.s * n3 * dgfs::real_size(p);
-  const size_t qb = size_t(batch) * p.s * p.s * n3 * dgfs::real_size(p);
+  const size_t qb = size_t(batch) * output_pairs(p) * n3 * dgfs::real_size(p);
   if (!p.d_stage_f) {
     const size_t fmax = size_t(p.max_batch) * p.s * n3 * dgfs::real_size(p);
-    const size_t qmax = fmax * p.s;
+    const size_t qmax = size_t(p.max_batch) * output_pairs(p) * n3 * dgfs::real_size(p);
     if (cudaMalloc(&p.d_stage_f, fmax) != cudaSuccess || cudaMalloc(&p.d_stage_Q, qmax) != cudaSuccess) {
       cudaGetLastError();
       if (p.d_stage_f) cudaFree(p.d_stage_f);
@@ -108,8 +123,7 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaMemcpyAsync(p.d_stage_f, f_host, fb, cudaMemcpyHostToDevice, st) != cudaSuccess) return DGFS_ERR_CUDA;
-  int rc = launch(p, p.d_stage_f, p.d_stage_Q, batch, st);
-  p.last_launches = rc == DGFS_OK ? 1 : 0;
+  const int rc = launch(p, p.d_stage_f, p.d_stage_Q, batch, st);
   if (rc != DGFS_OK) return rc;
   if (cudaMemcpyAsync(Q_host, p.d_stage_Q, qb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DGFS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return DGFS_ERR_CUDA;
@@ -122,7 +136,8 @@ int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace
   const size_t n3 = size_t(p.N) * p.N * p.N;
   if (tables) *tables = p.table_bytes;
   if (workspace)
-    *workspace = p.scratch_bytes + size_t(batch) * (p.s + p.s * p.s) * n3 * dgfs::real_size(p);
+    *workspace = p.scratch_bytes + (p.d_Qfull ? size_t(p.max_batch) * p.s * p.s * n3 * dgfs::real_size(p) : 0) +
+                 size_t(batch) * (p.s + output_pairs(p)) * n3 * dgfs::real_size(p);
   return DGFS_OK;
 }
 

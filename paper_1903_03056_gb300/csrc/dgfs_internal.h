@@ -41,6 +41,14 @@ struct KernelParams {
   int phase_smem;         // 1: the task's phase block of the current rho is staged in smem
 };
 
+// Conservation projection of one self pair (rows = 5) or one stacked cross pair (rows = 6):
+// constraint rows built from the grid, (C C^T)^-1 precomputed in FP64 on the host.
+struct ConsBlock {
+  int i, j, rows;
+  double a, b;        // m_i w_ij and m_j w_ji (cross pairs), w = 1 / b_ij
+  double minv[36];    // (C C^T)^-1, row-major rows x rows
+};
+
 struct LaunchShape {
   int cluster = 1;        // CTAs cooperating on one work item
   int groups = 1;         // plane groups per CTA
@@ -69,7 +77,13 @@ struct Plan {
   std::vector<int> ent_sigma;   // design index of each entry
   int max_ent = 0;
 
+  std::vector<double> kappa;       // species-sum weights [s*s]
+  std::vector<ConsBlock> cons;     // conservation blocks (DGFS_CONSERVE)
+
   // device tables
+  ConsBlock* d_cons = nullptr;
+  double* d_kappa = nullptr;
+  void* d_Qfull = nullptr;         // full operators staged for DGFS_SUM_SPECIES
   double* d_Fw = nullptr;
   double* d_Gm = nullptr;
   double* d_ent_w = nullptr;
@@ -100,5 +114,9 @@ int configure_f32(Plan& p);
 int configure_f64(Plan& p);
 int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+
+// conservation projection (in place on Q[batch][s][s][N^3]) and species sum (conserve.cu)
+int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st);
+int launch_species_sum(const Plan& p, const void* Qfull, void* Qsum, int batch, cudaStream_t st);
 
 }  // namespace dgfs

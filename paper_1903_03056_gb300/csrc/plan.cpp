@@ -112,13 +112,93 @@ static double sinc(double x) { return std::fabs(x) < 1e-300 ? 1.0 : std::sin(x) 
 
 static int centred_mode(int n, int N) { return n < N / 2 ? n : n - N; }
 
+// Gauss-Jordan inverse of a small symmetric positive definite matrix (FP64)
+static bool invert(int n, const double* a, double* inv) {
+  double m[6][12];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) m[r][c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(m[r][c]) > std::fabs(m[piv][c])) piv = r;
+    if (!(std::fabs(m[piv][c]) > 0.0)) return false;
+    for (int k = 0; k < 2 * n; ++k) std::swap(m[c][k], m[piv][k]);
+    const double d = m[c][c];
+    for (int k = 0; k < 2 * n; ++k) m[c][k] /= d;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double f = m[r][c];
+        for (int k = 0; k < 2 * n; ++k) m[r][k] -= f * m[c][k];
+      }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) inv[r * n + c] = m[r][n + c];
+  return true;
+}
+
+// Conservation blocks of Eq. consv on the cell-centred grid: for a self pair the rows
+// (1, v_x, v_y, v_z, |v|^2) acting on Q_ii; for a cross pair the rows acting on [Q_ij; Q_ji]:
+// mass of each half, (m_i w_ij v_d | m_j w_ji v_d), (m_i w_ij |v|^2 | m_j w_ji |v|^2), w = 1/b.
+static int build_conservation(Plan& p) {
+  const int N = p.N, s = p.s;
+  const double dv = 2.0 * p.L / N;
+  // grid moments sum_n v^a over one axis
+  double m0 = N, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+  for (int n = 0; n < N; ++n) {
+    const double v = -p.L + (n + 0.5) * dv;
+    m1 += v;
+    m2 += v * v;
+    m3 += v * v * v;
+    m4 += v * v * v * v;
+  }
+  const double N2 = double(N) * N, N3 = N2 * N;
+  // sums over the 3D grid of products of the basic rows 1, vx, vy, vz, |v|^2
+  double G[5][5] = {};
+  G[0][0] = N3;
+  for (int d = 0; d < 3; ++d) {
+    G[0][1 + d] = G[1 + d][0] = m1 * N2;
+    for (int e = 0; e < 3; ++e) G[1 + d][1 + e] = d == e ? m2 * N2 : m1 * m1 * N;
+    // sum vd |v|^2 = sum vd^3 N^2 + sum vd * (sum of the other two squares)
+    G[1 + d][4] = G[4][1 + d] = m3 * N2 + 2.0 * m1 * m2 * N;
+  }
+  G[0][4] = G[4][0] = 3.0 * m2 * N2;
+  G[4][4] = 3.0 * m4 * N2 + 6.0 * m2 * m2 * N;
+  for (int i = 0; i < s; ++i)
+    for (int j = i; j < s; ++j) {
+      ConsBlock cb{};
+      cb.i = i;
+      cb.j = j;
+      double A[36] = {};
+      if (i == j) {
+        cb.rows = 5;
+        for (int r = 0; r < 5; ++r)
+          for (int c = 0; c < 5; ++c) A[r * 5 + c] = G[r][c];
+      } else {
+        cb.rows = 6;
+        cb.a = p.mass[i] / p.b[i * s + j];
+        cb.b = p.mass[j] / p.b[j * s + i];
+        // row k of the stacked block = (alpha_k e_k | beta_k e_k) over the basic rows:
+        // k=0: (1 | 0), k=1: (0 | 1), k=2..4: (a v | b v), k=5: (a |v|^2 | b |v|^2)
+        const int basic[6] = {0, 0, 1, 2, 3, 4};
+        const double al[6] = {1.0, 0.0, cb.a, cb.a, cb.a, cb.a};
+        const double be[6] = {0.0, 1.0, cb.b, cb.b, cb.b, cb.b};
+        for (int r = 0; r < 6; ++r)
+          for (int c = 0; c < 6; ++c)
+            A[r * 6 + c] = (al[r] * al[c] + be[r] * be[c]) * G[basic[r]][basic[c]];
+      }
+      if (!invert(cb.rows, A, cb.minv)) return DGFS_ERR_INVALID_ARG;
+      p.cons.push_back(cb);
+    }
+  return DGFS_OK;
+}
+
 int build_plan(const dgfs_plan_desc* d, Plan& p) {
   if (!d) return DGFS_ERR_INVALID_ARG;
   if (!supported_n(d->N)) return DGFS_ERR_UNSUPPORTED_N;
   if (!(d->L > 0.0) || d->s < 1 || d->s > 8 || !d->mass || !d->omega || !d->alpha) return DGFS_ERR_INVALID_ARG;
   if (d->N_rho < 1 || d->N_rho > 4096 || d->M < 1 || d->max_batch < 0) return DGFS_ERR_INVALID_ARG;
   if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32) return DGFS_ERR_INVALID_ARG;
-  if (d->flags != 0u) return DGFS_ERR_UNSUPPORTED;
+  if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES)) != 0u) return DGFS_ERR_INVALID_ARG;
   const int s = d->s;
   p.N = d->N;
   p.L = d->L;
@@ -137,6 +217,12 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     if (!(p.alpha[k] >= 1.0 && p.alpha[k] <= 2.0)) return DGFS_ERR_INVALID_ARG;
     if (p.alpha[k] != 1.0) return DGFS_ERR_UNSUPPORTED;  // VSS gain weights: not in this build
   }
+  p.kappa.assign(s * s, 1.0);
+  if (d->kappa)
+    for (int k = 0; k < s * s; ++k) {
+      if (!std::isfinite(d->kappa[k])) return DGFS_ERR_INVALID_ARG;
+      p.kappa[k] = d->kappa[k];
+    }
   p.b.assign(s * s, 0.0);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j)
@@ -248,6 +334,11 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
       p.tasks.push_back(tk);
     }
   }
+  if (p.flags & DGFS_CONSERVE) {
+    for (int k = 0; k < s * s; ++k)
+      if (!(std::fabs(p.b[k]) > 0.0)) return DGFS_ERR_INVALID_ARG;
+    if (int rc = build_conservation(p)) return rc;
+  }
   return DGFS_OK;
 }
 
@@ -341,7 +432,17 @@ int upload_plan(Plan& p) {
     }
     if ((rc = upload(phd.data(), phd.size(), &p.d_phase, total))) return rc;
   }
+  if ((rc = upload(p.kappa.data(), p.kappa.size(), (void**)&p.d_kappa, total))) return rc;
+  if (!p.cons.empty() && (rc = upload(p.cons.data(), p.cons.size(), (void**)&p.d_cons, total))) return rc;
   p.table_bytes = total;
+  if ((p.flags & DGFS_SUM_SPECIES) && p.max_batch > 0) {
+    const size_t qb = size_t(p.max_batch) * s * s * N3 * real_size(p);
+    if (cudaMalloc(&p.d_Qfull, qb) != cudaSuccess) {
+      cudaGetLastError();
+      p.d_Qfull = nullptr;
+      return DGFS_ERR_OOM;
+    }
+  }
   if (cudaMalloc(&p.d_scratch, p.scratch_bytes) != cudaSuccess) {
     cudaGetLastError();
     p.d_scratch = nullptr;
@@ -351,13 +452,17 @@ int upload_plan(Plan& p) {
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_Fw, p.d_Gm, p.d_ent_w, p.d_phase, p.d_tasks, p.d_groups, p.d_scratch, p.d_stage_f, p.d_stage_Q};
+  void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups,
+                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p.d_Fw = p.d_Gm = p.d_ent_w = nullptr;
   p.d_phase = p.d_scratch = p.d_stage_f = p.d_stage_Q = nullptr;
   p.d_tasks = nullptr;
   p.d_groups = nullptr;
+  p.d_cons = nullptr;
+  p.d_kappa = nullptr;
+  p.d_Qfull = nullptr;
 }
 
 }  // namespace dgfs

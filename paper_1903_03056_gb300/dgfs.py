@@ -26,6 +26,8 @@ DGFS_ERR_DEVICE_TIMEOUT = -6
 DGFS_ERR_UNSUPPORTED = -7
 DGFS_FP64 = 0
 DGFS_FP32 = 1
+DGFS_CONSERVE = 1
+DGFS_SUM_SPECIES = 2
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
@@ -39,7 +41,7 @@ class dgfs_plan_desc(ctypes.Structure):
                 ("mass", _dptr), ("omega", _dptr), ("alpha", _dptr), ("b_override", _dptr),
                 ("M", ctypes.c_int), ("sigma", _dptr), ("w_sigma", _dptr),
                 ("N_rho", ctypes.c_int), ("R", ctypes.c_double), ("precision", ctypes.c_int),
-                ("flags", ctypes.c_uint), ("max_batch", ctypes.c_int)]
+                ("flags", ctypes.c_uint), ("max_batch", ctypes.c_int), ("kappa", _dptr)]
 
 
 class DgfsError(RuntimeError):
@@ -136,7 +138,7 @@ def _arr(x, n):
 
 
 def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision="fp32",
-              b_override=None, sigma=None, w_sigma=None, max_batch=0):
+              b_override=None, sigma=None, w_sigma=None, max_batch=0, flags=0, kappa=None):
     """Build a dgfs_plan_desc; returns (desc, keepalive) -- keep the second alive until the
     plan is created."""
     s = len(masses)
@@ -165,8 +167,12 @@ def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision
     d.N_rho = int(N if N_rho is None else N_rho)
     d.R = float(R)
     d.precision = DGFS_FP32 if precision in ("fp32", DGFS_FP32) else DGFS_FP64
-    d.flags = 0
+    d.flags = int(flags)
     d.max_batch = int(max_batch)
+    if kappa is not None:
+        ka, pk = _arr(np.asarray(kappa, dtype=np.float64).reshape(-1), s * s)
+        keep.append(ka)
+        d.kappa = pk
     return d, keep
 
 
@@ -190,6 +196,7 @@ class Plan:
         self.N, self.L, self.s = int(N), float(L), len(masses)
         self.precision = kw.get("precision", "fp32")
         self.max_batch = int(kw.get("max_batch", 0))
+        self.flags = int(kw.get("flags", 0))
 
     @property
     def dtype_name(self):
@@ -220,7 +227,8 @@ class Plan:
         assert f.is_cuda and f.is_contiguous() and str(f.dtype).endswith(self.dtype_name)
         B = f.shape[0]
         if Q is None:
-            Q = torch.empty((B, self.s, self.s) + tuple(f.shape[2:]), dtype=f.dtype, device=f.device)
+            pairs = (self.s,) if self.flags & DGFS_SUM_SPECIES else (self.s, self.s)
+            Q = torch.empty((B,) + pairs + tuple(f.shape[2:]), dtype=f.dtype, device=f.device)
         self.eval_ptr(f.data_ptr(), Q.data_ptr(), B, stream)
         return Q
 

@@ -326,3 +326,43 @@ def test_reflection_symmetry():
     Q, _ = fs.collision(f, prob)
     Qr, _ = fs.collision(f[:, ::-1].copy(), prob)
     assert np.max(np.abs(Qr[:, :, ::-1] - Q)) < 1e-12 * np.max(np.abs(Q))
+
+
+# ---------------------------------------------------------------- conservation projection
+
+def _projection_case():
+    N, L, masses = 8, 5.0, [1.0, 2.5, 4.0]
+    b = np.array([[0.11, 0.07, 0.05], [0.09, 0.13, 0.04], [0.03, 0.06, 0.08]])
+    Q = np.random.default_rng(4).normal(size=(3, 3, N, N, N))
+    return N, L, masses, b, Q
+
+
+def test_projection_makes_conservation_exact_and_is_idempotent():
+    N, L, masses, b, Q = _projection_case()
+    Qc = moments.conservation_projection(Q, masses, L, b)
+    r = moments.conservation_residuals(Qc, masses, L, kappa=1.0 / b)
+    assert np.max(np.abs(r["mass"]) / r["mass_scale"]) < 1e-13
+    assert np.max(np.linalg.norm(r["momentum"], axis=-1) / r["momentum_scale"]) < 1e-13
+    assert np.max(np.abs(r["energy"]) / r["energy_scale"]) < 1e-13
+    assert np.max(np.abs(moments.conservation_projection(Qc, masses, L, b) - Qc)) < 1e-12
+
+
+def test_projection_is_the_nearest_conservative_operator():
+    """Any other Q' satisfying the laws is at least as far from Q (per block, L2)."""
+    N, L, masses, b, Q = _projection_case()
+    Qc = moments.conservation_projection(Q, masses, L, b)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        other = moments.conservation_projection(Q + rng.normal(size=Q.shape), masses, L, b)
+        for i in range(3):
+            for j in range(i, 3):
+                blk = (lambda A: A[i, i].ravel()) if i == j else (
+                    lambda A: np.concatenate([A[i, j].ravel(), A[j, i].ravel()]))
+                assert np.linalg.norm(blk(Qc) - blk(Q)) <= np.linalg.norm(blk(other) - blk(Q)) + 1e-12
+
+
+def test_species_sum_definition():
+    Q = np.random.default_rng(1).normal(size=(2, 2, 4, 4, 4))
+    k = np.array([[1.0, 2.0], [3.0, 4.0]])
+    S = moments.species_sum(Q, k)
+    assert np.allclose(S[0], Q[0, 0] + 2 * Q[0, 1]) and np.allclose(S[1], 3 * Q[1, 0] + 4 * Q[1, 1])

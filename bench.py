@@ -13,6 +13,7 @@ no collective on the data path).
 
 import argparse
 import json
+import math
 import multiprocessing as mp
 import os
 import statistics
@@ -201,6 +202,28 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
     return ms / steps
 
 
+def serving_leg(args):
+    """The mixed request stream: N in {16, 24, 32, 48}, s in {2, 3}, masses U[1, 4], VHS
+    omega U[0.5, 1], batches of 1..4096 nodes, FP32, 120 GB HBM budget, 8 slots.  A closed-loop
+    run of the first requests measures the mix's throughput; the Poisson stream then arrives
+    at 75% of it."""
+    from paper_1903_03056_gb300 import serve
+    budget = 120 << 30
+    ex = serve.GpuExecutor(slots=8)
+    eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8)
+    calib = serve.mixed_stream(args.serve_calib, math.inf, seed=5000)
+    st0 = eng.run(calib)
+    rate = 0.75 * st0.n / st0.makespan
+    stream = serve.mixed_stream(args.serve_requests, rate, seed=5001)
+    st = eng.run(stream)
+    out = st.as_dict()
+    out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
+                "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
+                "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
+                       "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
+    return out
+
+
 def gpu_arm(args):
     import torch
     from paper_1903_03056_gb300 import build, dgfs, synth
@@ -278,6 +301,13 @@ def gpu_arm(args):
                 "steps": args.fp64_steps, "dtype": "f64",
                 "mixed_over_fp64": value / (world * B / (ms64 * 1e-3))}
         plan64.close()
+        del fd, Qd
+
+    serving = None
+    if not args.no_serving and world == 1:
+        del f32
+        torch.cuda.empty_cache()
+        serving = serving_leg(args)
 
     if rank == 0:
         achieved = flops_node * B / (ms32 * 1e-3) / 1e12
@@ -292,7 +322,7 @@ def gpu_arm(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_dict(w), "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "fp64": fp64}
+                "clocks": clk.summary(), "fp64": fp64, "serving": serving}
         print(json.dumps(line), flush=True)
     plan32.close()
     if dist is not None:
@@ -308,6 +338,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-calib", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

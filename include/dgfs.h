@@ -82,11 +82,14 @@ typedef struct {
 } dgfs_plan_desc;
 
 /* Build the tables (Gauss-Legendre rule, design, b_ij of Eq. NVSS, R of Eq. domain, gain
- * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), all FP64) and the
- * workspace on the current device.  *out receives the plan.  Synchronous. */
+ * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), all FP64, the N^3-sized
+ * ones computed on the device) and the workspace on the current device.  *out receives the
+ * plan.  Device memory is allocated stream-ordered on a stream the plan owns; the call
+ * returns when the plan is ready and never synchronises other streams. */
 int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out);
 
-/* Release the plan's device memory.  Waits for the device to finish using it. */
+/* Release the plan's device memory.  Waits for the plan's most recent evaluation (not for
+ * the rest of the device) and frees stream-ordered. */
 int dgfs_destroy_plan(dgfs_plan plan);
 
 /* Q = all s^2 collision operators of the batch (Sec. 4), device pointers, stream-ordered.

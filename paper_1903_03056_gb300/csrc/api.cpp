@@ -45,10 +45,11 @@ int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
     if ((rc = dgfs::launch_species_sum(p, Qfull, Q, batch, st)) != DGFS_OK) return rc;
     p.last_launches += 1;
   }
-  if (cudaPeekAtLastError() != cudaSuccess) {
+  if (cudaEventRecord(p.last_eval, st) != cudaSuccess || cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return DGFS_ERR_CUDA;
   }
+  p.has_eval = true;
   return DGFS_OK;
 }
 
@@ -82,7 +83,8 @@ int dgfs_destroy_plan(dgfs_plan plan) {
   if (!plan) return DGFS_ERR_INVALID_ARG;
   {
     DeviceGuard g(plan->plan.device);
-    cudaDeviceSynchronize();
+    // wait for the plan's last evaluation only; other streams keep running
+    if (plan->plan.has_eval) cudaEventSynchronize(plan->plan.last_eval);
     dgfs::free_plan(plan->plan);
   }
   delete plan;
@@ -112,9 +114,12 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   if (!p.d_stage_f) {
     const size_t fmax = size_t(p.max_batch) * p.s * n3 * dgfs::real_size(p);
     const size_t qmax = size_t(p.max_batch) * output_pairs(p) * n3 * dgfs::real_size(p);
-    if (cudaMalloc(&p.d_stage_f, fmax) != cudaSuccess || cudaMalloc(&p.d_stage_Q, qmax) != cudaSuccess) {
+    if (cudaMallocAsync(&p.d_stage_f, fmax, p.home) != cudaSuccess ||
+        cudaMallocAsync(&p.d_stage_Q, qmax, p.home) != cudaSuccess || cudaStreamSynchronize(p.home) != cudaSuccess) {
       cudaGetLastError();
-      if (p.d_stage_f) cudaFree(p.d_stage_f);
+      if (p.d_stage_f) cudaFreeAsync(p.d_stage_f, p.home);
+      if (p.d_stage_Q) cudaFreeAsync(p.d_stage_Q, p.home);
+      cudaStreamSynchronize(p.home);
       p.d_stage_f = nullptr;
       p.d_stage_Q = nullptr;
       return DGFS_ERR_OOM;

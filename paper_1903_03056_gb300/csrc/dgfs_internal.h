@@ -60,6 +60,9 @@ struct LaunchShape {
 
 struct Plan {
   int device = 0;
+  cudaStream_t home = nullptr;     // the plan's own stream: table builds, stream-ordered alloc/free
+  cudaEvent_t last_eval = nullptr; // recorded after every evaluation
+  bool has_eval = false;
   int N = 0;
   double L = 0;
   int s = 0;
@@ -114,6 +117,9 @@ int configure_f32(Plan& p);
 int configure_f64(Plan& p);
 int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+
+// on-device FP64 VHS weight tables on the plan's stream (tables.cu)
+int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale);
 
 // conservation projection (in place on Q[batch][s][s][N^3]) and species sum (conserve.cu)
 int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st);

@@ -108,8 +108,6 @@ static double vss_prefactor(double mi, double mj, double omega, double alpha) {
                   std::tgamma(2.5 - omega) * kPi);
 }
 
-static double sinc(double x) { return std::fabs(x) < 1e-300 ? 1.0 : std::sin(x) / x; }
-
 static int centred_mode(int n, int N) { return n < N / 2 ? n : n - N; }
 
 // Gauss-Jordan inverse of a small symmetric positive definite matrix (FP64)
@@ -342,50 +340,50 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   return DGFS_OK;
 }
 
-template <typename V>
-static int upload(const V* host, size_t count, void** dptr, size_t& total) {
-  const size_t bytes = count * sizeof(V);
-  if (cudaMalloc(dptr, bytes) != cudaSuccess) {
+static int dalloc(Plan& p, void** dptr, size_t bytes) {
+  if (cudaMallocAsync(dptr, bytes, p.home) != cudaSuccess) {
     cudaGetLastError();
     *dptr = nullptr;
     return DGFS_ERR_OOM;
   }
-  if (cudaMemcpy(*dptr, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return DGFS_ERR_CUDA;
+  return DGFS_OK;
+}
+
+template <typename V>
+static int upload(Plan& p, const V* host, size_t count, void** dptr, size_t& total) {
+  const size_t bytes = count * sizeof(V);
+  if (int rc = dalloc(p, dptr, bytes)) return rc;
+  if (cudaMemcpyAsync(*dptr, host, bytes, cudaMemcpyHostToDevice, p.home) != cudaSuccess) return DGFS_ERR_CUDA;
   total += bytes;
   return DGFS_OK;
 }
 
+// Device memory of the plan is stream-ordered on the plan's own stream (cudaMallocAsync /
+// cudaFreeAsync), so creating and destroying plans never synchronises other streams; the
+// function returns after the plan's stream has finished the uploads and table builds.
 int upload_plan(Plan& p) {
   const int N = p.N, s = p.s, NR = p.N_rho;
   const size_t N3 = size_t(N) * N * N;
   const int P = s * s;
-  // |k| on the FFT-ordered grid (x slowest, z fastest)
-  std::vector<double> kabs(N3);
-  for (int a = 0; a < N; ++a)
-    for (int b = 0; b < N; ++b)
-      for (int c = 0; c < N; ++c) {
-        const double kx = centred_mode(a, N), ky = centred_mode(b, N), kz = centred_mode(c, N);
-        kabs[(size_t(a) * N + b) * N + c] = std::sqrt(kx * kx + ky * ky + kz * kz);
-      }
-  // gain weights w_rho F^(ij)(k, rho) / N^3 with F = 4 pi b rho^(4-2 omega) sinc(pi rho c_j |k| / L)
-  // (VHS form of Eq. GG) and loss weights G^(ij)-(k) = 16 pi^2 b sum_q w_q rho_q^(4-2 omega)
-  // sinc(pi rho_q |k| / L) on the same radial rule
-  std::vector<double> Fw(size_t(P) * NR * N3), Gm(size_t(P) * N3, 0.0);
+  if (!p.home && cudaStreamCreateWithFlags(&p.home, cudaStreamNonBlocking) != cudaSuccess) return DGFS_ERR_CUDA;
+  if (!p.last_eval && cudaEventCreateWithFlags(&p.last_eval, cudaEventDisableTiming) != cudaSuccess)
+    return DGFS_ERR_CUDA;
+  // per (pair, rho) constants of the weight tables: gain prefactor and sinc scale, loss
+  // prefactor; the sinc scale of the loss depends on rho only
+  std::vector<double> fcoef(size_t(P) * NR * 2), gcoef(size_t(P) * NR), gscale(NR);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
       const int o = i * s + j;
       const double b = p.b[o], om = p.omega[o];
       const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
       for (int q = 0; q < NR; ++q) {
-        const double rho = p.rho[q];
-        const double pref = p.w_rho[q] * 4.0 * kPi * b * std::pow(rho, 4.0 - 2.0 * om) / double(N3);
-        double* dst = &Fw[(size_t(o) * NR + q) * N3];
-        for (size_t n = 0; n < N3; ++n) dst[n] = pref * sinc(kPi * rho * cj * kabs[n] / p.L);
-        const double gpref = 16.0 * kPi * kPi * b * p.w_rho[q] * std::pow(rho, 4.0 - 2.0 * om);
-        double* g = &Gm[size_t(o) * N3];
-        for (size_t n = 0; n < N3; ++n) g[n] += gpref * sinc(kPi * rho * kabs[n] / p.L);
+        const double rp = std::pow(p.rho[q], 4.0 - 2.0 * om);
+        fcoef[2 * (size_t(o) * NR + q)] = p.w_rho[q] * 4.0 * kPi * b * rp / double(N3);
+        fcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
+        gcoef[size_t(o) * NR + q] = 16.0 * kPi * kPi * b * p.w_rho[q] * rp;
       }
     }
+  for (int q = 0; q < NR; ++q) gscale[q] = kPi * p.rho[q] / p.L;
   // phase factors exp(i pi shift_d k / L) per task, radial node, entry, role, axis
   const int NT = int(p.tasks.size());
   const size_t nph = size_t(NT) * NR * p.max_ent * 2 * 3 * N;
@@ -410,52 +408,71 @@ int upload_plan(Plan& p) {
         }
       }
   }
-  size_t total = 0;
-  int rc;
-  if ((rc = upload(Fw.data(), Fw.size(), (void**)&p.d_Fw, total))) return rc;
-  if ((rc = upload(Gm.data(), Gm.size(), (void**)&p.d_Gm, total))) return rc;
-  if ((rc = upload(p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
-  if ((rc = upload(p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
-  if ((rc = upload(p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
+  std::vector<float> phf;
+  std::vector<double> phd;
   if (p.precision == DGFS_FP32) {
-    std::vector<float> phf(2 * nph);
+    phf.resize(2 * nph);
     for (size_t n = 0; n < nph; ++n) {
       phf[2 * n] = float(ph[n].real());
       phf[2 * n + 1] = float(ph[n].imag());
     }
-    if ((rc = upload(phf.data(), phf.size(), &p.d_phase, total))) return rc;
   } else {
-    std::vector<double> phd(2 * nph);
+    phd.resize(2 * nph);
     for (size_t n = 0; n < nph; ++n) {
       phd[2 * n] = ph[n].real();
       phd[2 * n + 1] = ph[n].imag();
     }
-    if ((rc = upload(phd.data(), phd.size(), &p.d_phase, total))) return rc;
   }
-  if ((rc = upload(p.kappa.data(), p.kappa.size(), (void**)&p.d_kappa, total))) return rc;
-  if (!p.cons.empty() && (rc = upload(p.cons.data(), p.cons.size(), (void**)&p.d_cons, total))) return rc;
+  size_t total = 0;
+  int rc;
+  void *d_fcoef = nullptr, *d_gcoef = nullptr, *d_gscale = nullptr;
+  size_t tmp = 0;
+  if ((rc = dalloc(p, (void**)&p.d_Fw, size_t(P) * NR * N3 * sizeof(double)))) return rc;
+  if ((rc = dalloc(p, (void**)&p.d_Gm, size_t(P) * N3 * sizeof(double)))) return rc;
+  total += (size_t(P) * NR * N3 + size_t(P) * N3) * sizeof(double);
+  if ((rc = upload(p, fcoef.data(), fcoef.size(), &d_fcoef, tmp))) return rc;
+  if ((rc = upload(p, gcoef.data(), gcoef.size(), &d_gcoef, tmp))) return rc;
+  if ((rc = upload(p, gscale.data(), gscale.size(), &d_gscale, tmp))) return rc;
+  if ((rc = launch_vhs_tables(p, static_cast<double*>(d_fcoef), static_cast<double*>(d_gcoef),
+                              static_cast<double*>(d_gscale))))
+    return rc;
+  cudaFreeAsync(d_fcoef, p.home);
+  cudaFreeAsync(d_gcoef, p.home);
+  cudaFreeAsync(d_gscale, p.home);
+  if ((rc = upload(p, p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
+  if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
+  if ((rc = upload(p, p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
+  if (p.precision == DGFS_FP32) {
+    if ((rc = upload(p, phf.data(), phf.size(), &p.d_phase, total))) return rc;
+  } else {
+    if ((rc = upload(p, phd.data(), phd.size(), &p.d_phase, total))) return rc;
+  }
+  if ((rc = upload(p, p.kappa.data(), p.kappa.size(), (void**)&p.d_kappa, total))) return rc;
+  if (!p.cons.empty() && (rc = upload(p, p.cons.data(), p.cons.size(), (void**)&p.d_cons, total))) return rc;
   p.table_bytes = total;
   if ((p.flags & DGFS_SUM_SPECIES) && p.max_batch > 0) {
-    const size_t qb = size_t(p.max_batch) * s * s * N3 * real_size(p);
-    if (cudaMalloc(&p.d_Qfull, qb) != cudaSuccess) {
-      cudaGetLastError();
-      p.d_Qfull = nullptr;
-      return DGFS_ERR_OOM;
-    }
+    if ((rc = dalloc(p, &p.d_Qfull, size_t(p.max_batch) * s * s * N3 * real_size(p)))) return rc;
   }
-  if (cudaMalloc(&p.d_scratch, p.scratch_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    p.d_scratch = nullptr;
-    return DGFS_ERR_OOM;
-  }
+  if ((rc = dalloc(p, &p.d_scratch, p.scratch_bytes))) return rc;
+  // the host arrays above must outlive the copies
+  if (cudaStreamSynchronize(p.home) != cudaSuccess) return DGFS_ERR_CUDA;
   return DGFS_OK;
 }
 
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups,
                   p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  if (p.home) {
+    for (void* q : ptrs)
+      if (q) cudaFreeAsync(q, p.home);
+    cudaStreamSynchronize(p.home);
+    cudaStreamDestroy(p.home);
+    p.home = nullptr;
+  }
+  if (p.last_eval) {
+    cudaEventDestroy(p.last_eval);
+    p.last_eval = nullptr;
+  }
   p.d_Fw = p.d_Gm = p.d_ent_w = nullptr;
   p.d_phase = p.d_scratch = p.d_stage_f = p.d_stage_Q = nullptr;
   p.d_tasks = nullptr;

@@ -1,0 +1,313 @@
+"""Serving: a continuous-batching request loop over the collision library.
+
+A request asks for the s^2 collision operators of a batch of DG nodes on a velocity grid of
+its own (N, L, masses, omega, M, N_rho).  Node states live on the device (in a DG solver the
+operator feeds the next Runge-Kutta stage there), so a request arrives with its input f in
+device memory and completes when its Q is in device memory.
+
+Loop (one host thread, ``ServingEngine.run``):
+
+* arrival -- the request enters the pending queue and its plan is built on a worker thread
+  (tables are computed on the device on the plan's own stream; plans with identical
+  parameters are shared through a cache);
+* admission -- in arrival order, a pending request whose plan is ready is admitted when a
+  slot (a CUDA stream) is free and the HBM budget covers its plan, its input copy and its
+  output; requests that arrive while others run are admitted as soon as slots and memory
+  free up, so their kernels overlap on the device;
+* completion -- an event per request; on completion the slot and the memory are released.
+
+The budget covers admitted requests (plan tables, workspace, input and output); plans built
+ahead for waiting requests are bounded by the prefetch depth.
+
+Latency = completion - arrival.  The executor is pluggable: ``GpuExecutor`` drives the CUDA
+library, ``FakeExecutor`` (tests) models durations on the CPU.
+"""
+
+import collections
+import math
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+L_FOR_N = {8: 4.0, 12: 5.0, 16: 6.0, 24: 6.0, 32: 7.0, 48: 8.0}
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    N: int
+    L: float
+    masses: tuple
+    omega: float
+    M: int
+    N_rho: int
+    batch: int
+    pool_offset: int = 0    # first node of the input pool tiled into this request
+    admitted: float = None
+    done: float = None
+    bytes: int = 0
+    slot: int = -1
+
+    @property
+    def s(self):
+        return len(self.masses)
+
+    @property
+    def plan_key(self):
+        return (self.N, self.L, self.masses, self.omega, self.M, self.N_rho)
+
+    @property
+    def latency(self):
+        return None if self.done is None else self.done - self.arrival
+
+
+def mixed_stream(n_requests, rate, seed=5000, sizes=(16, 24, 32, 48), max_batch=4096):
+    """Seeded request mix: N uniform over `sizes`, s in {2, 3}, masses U[1, 4], one VHS
+    omega U[0.5, 1] for all pairs, M = 12, N_rho = N/2, batch = round(exp U[0, ln max_batch]),
+    Poisson arrivals at `rate` requests/s (rate = inf: all at t = 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for k in range(n_requests):
+        if math.isfinite(rate):
+            t += rng.exponential(1.0 / rate)
+        N = int(rng.choice(sizes))
+        s = int(rng.integers(2, 4))
+        masses = tuple(float(m) for m in np.round(rng.uniform(1.0, 4.0, size=s), 6))
+        omega = float(np.round(rng.uniform(0.5, 1.0), 6))
+        batch = int(max(1, min(max_batch, round(math.exp(rng.uniform(0.0, math.log(max_batch)))))))
+        out.append(Request(k, t if math.isfinite(rate) else 0.0, N, L_FOR_N[N], masses, omega, 12,
+                           N // 2, batch, pool_offset=int(rng.integers(0, 1 << 20))))
+    return out
+
+
+def percentile(values, p):
+    v = sorted(values)
+    if not v:
+        return None
+    k = (len(v) - 1) * p / 100.0
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+@dataclass
+class Stats:
+    n: int
+    nodes: int
+    makespan: float
+    p50: float
+    p99: float
+    mean_latency: float
+    peak_bytes: int
+    peak_inflight: int
+    budget: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def evals_per_s(self):
+        return self.nodes / self.makespan if self.makespan > 0 else 0.0
+
+    def as_dict(self):
+        d = {"requests": self.n, "nodes": self.nodes, "makespan_s": self.makespan,
+             "evals_per_s": self.evals_per_s, "p50_ms": self.p50 * 1e3, "p99_ms": self.p99 * 1e3,
+             "mean_ms": self.mean_latency * 1e3, "peak_bytes": self.peak_bytes,
+             "peak_inflight": self.peak_inflight, "budget_bytes": self.budget}
+        d.update(self.extra)
+        return d
+
+
+class ServingEngine:
+    def __init__(self, executor, budget_bytes, slots=8, prefetch=8):
+        self.ex = executor
+        self.budget = int(budget_bytes)
+        self.slots = slots
+        self.prefetch = prefetch
+
+    def run(self, requests, poll_s=50e-6):
+        """Serve `requests` (arrival times relative to the start); returns Stats."""
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        arrivals = collections.deque(reqs)
+        pending = collections.deque()       # arrived, waiting for admission (FIFO)
+        plans = {}                          # rid -> future of the plan
+        inflight = {}                       # slot -> request
+        free_slots = list(range(self.slots))
+        in_use = 0
+        peak_bytes, peak_inflight = 0, 0
+        builder = ThreadPoolExecutor(max_workers=2)
+        t0 = time.perf_counter()
+        try:
+            while arrivals or pending or inflight:
+                now = time.perf_counter() - t0
+                while arrivals and arrivals[0].arrival <= now:
+                    pending.append(arrivals.popleft())
+                # build plans for the first few waiting requests, in arrival order
+                for r in list(pending)[: self.prefetch]:
+                    if r.rid not in plans:
+                        plans[r.rid] = builder.submit(self.ex.prepare, r)
+                # admission in arrival order: the head must fit before later requests go
+                while pending and free_slots:
+                    r = pending[0]
+                    fut = plans.get(r.rid)
+                    if fut is None or not fut.done():
+                        break
+                    need = fut.result()
+                    if need > self.budget:
+                        raise RuntimeError("request %d needs %d bytes, budget %d" % (r.rid, need, self.budget))
+                    if in_use + need > self.budget:
+                        break
+                    pending.popleft()
+                    slot = free_slots.pop()
+                    r.slot, r.bytes = slot, need
+                    r.admitted = time.perf_counter() - t0
+                    in_use += need
+                    self.ex.submit(r, slot)
+                    inflight[slot] = r
+                    peak_bytes = max(peak_bytes, in_use)
+                    peak_inflight = max(peak_inflight, len(inflight))
+                # completions
+                for slot, r in list(inflight.items()):
+                    if self.ex.done(r):
+                        r.done = time.perf_counter() - t0
+                        self.ex.release(r)
+                        plans.pop(r.rid, None)
+                        in_use -= r.bytes
+                        del inflight[slot]
+                        free_slots.append(slot)
+                if not inflight and not pending and arrivals:
+                    wait = arrivals[0].arrival - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                else:
+                    time.sleep(poll_s)
+        finally:
+            builder.shutdown(wait=True)
+        lat = [r.latency for r in reqs]
+        first = min(r.arrival for r in reqs)
+        makespan = max(r.done for r in reqs) - first
+        return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=makespan,
+                     p50=percentile(lat, 50), p99=percentile(lat, 99),
+                     mean_latency=sum(lat) / len(lat), peak_bytes=peak_bytes,
+                     peak_inflight=peak_inflight, budget=self.budget)
+
+
+class FakeExecutor:
+    """CPU model of the device for scheduler tests: a request occupies its slot for
+    `seconds_per_node * batch` and needs a fixed number of bytes per node."""
+
+    def __init__(self, seconds_per_node=1e-5, bytes_per_node=1 << 20, plan_bytes=1 << 24):
+        self.spn, self.bpn, self.pb = seconds_per_node, bytes_per_node, plan_bytes
+        self.lock = threading.Lock()
+        self.active = 0
+        self.max_active = 0
+        self.log = []
+
+    def prepare(self, r):
+        return self.pb + self.bpn * r.batch
+
+    def submit(self, r, slot):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+            self.log.append(("submit", r.rid, slot))
+        r._t_end = time.perf_counter() + self.spn * r.batch
+
+    def done(self, r):
+        return time.perf_counter() >= r._t_end
+
+    def release(self, r):
+        with self.lock:
+            self.active -= 1
+            self.log.append(("release", r.rid, r.slot))
+
+
+class GpuExecutor:
+    """Drives libdgfs: plans from a cache (shared by requests with equal parameters), one
+    CUDA stream per slot, device-resident inputs tiled from a seeded node pool."""
+
+    def __init__(self, slots=8, precision="fp32", pool_nodes=32, keep_outputs=False, device=0):
+        import torch
+
+        from . import dgfs, synth
+        self.torch, self.dgfs, self.synth = torch, dgfs, synth
+        self.dev = torch.device("cuda", device)
+        self.dt = torch.float32 if precision == "fp32" else torch.float64
+        self.precision = precision
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
+        self.pool_nodes = pool_nodes
+        self.pools = {}
+        self.plans = {}
+        self.plan_users = collections.Counter()
+        self.lock = threading.Lock()
+        self.keep_outputs = keep_outputs
+        self.outputs = {}
+        self.state = {}
+
+    def _pool(self, N, s):
+        """Seeded input nodes per (N, s), on the device (bi-Maxwellians with 5% noise)."""
+        key = (N, s)
+        if key not in self.pools:
+            w = self.synth.Workload("serving pool", self.pool_nodes, N, L_FOR_N[N],
+                                    tuple([1.0] * s), 0.75, 1.0, 12, N // 2, "bimaxwellian", 0.05,
+                                    9000 + 100 * N + s)
+            f = self.synth.batch_distribution(w)
+            self.pools[key] = self.torch.from_numpy(f).to(device=self.dev, dtype=self.dt)
+        return self.pools[key]
+
+    def prepare(self, r):
+        torch = self.torch
+        with torch.cuda.device(self.dev):
+            with self.lock:
+                plan = self.plans.get(r.plan_key)
+                if plan is None:
+                    plan = self.dgfs.Plan(r.N, r.L, list(r.masses), r.omega, M=r.M, N_rho=r.N_rho,
+                                          precision=self.precision)
+                    self.plans[r.plan_key] = plan
+                self.plan_users[r.plan_key] += 1
+            self._pool(r.N, r.s)
+        tables, work = plan.bytes(0)
+        esz = 4 if self.precision == "fp32" else 8
+        n3 = r.N ** 3
+        return tables + work + r.batch * (r.s + r.s * r.s) * n3 * esz
+
+    def submit(self, r, slot):
+        torch = self.torch
+        st = self.streams[slot]
+        plan = self.plans[r.plan_key]
+        pool = self._pool(r.N, r.s)
+        with torch.cuda.stream(st):
+            idx = (torch.arange(r.batch, device=self.dev) + r.pool_offset) % self.pool_nodes
+            f = pool.index_select(0, idx)
+            Q = torch.empty((r.batch, r.s, r.s, r.N, r.N, r.N), dtype=self.dt, device=self.dev)
+            plan.eval_ptr(f.data_ptr(), Q.data_ptr(), r.batch, st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        self.state[r.rid] = (f, Q, ev)
+
+    def done(self, r):
+        return self.state[r.rid][2].query()
+
+    def release(self, r):
+        f, Q, ev = self.state.pop(r.rid)
+        if self.keep_outputs:
+            self.outputs[r.rid] = Q
+        with self.lock:
+            self.plan_users[r.plan_key] -= 1
+            if self.plan_users[r.plan_key] == 0:
+                self.plans.pop(r.plan_key).close()
+                del self.plan_users[r.plan_key]
+
+    def run_alone(self, r):
+        """Evaluate one request by itself (fresh plan, default stream); returns Q."""
+        torch = self.torch
+        plan = self.dgfs.Plan(r.N, r.L, list(r.masses), r.omega, M=r.M, N_rho=r.N_rho,
+                              precision=self.precision)
+        pool = self._pool(r.N, r.s)
+        idx = (torch.arange(r.batch, device=self.dev) + r.pool_offset) % self.pool_nodes
+        Q = plan.eval(pool.index_select(0, idx).contiguous())
+        torch.cuda.synchronize()
+        plan.close()
+        return Q

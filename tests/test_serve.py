@@ -1,0 +1,68 @@
+"""Serving loop: admission by slots and HBM budget, arrival order, latency statistics (CPU,
+fake executor), and on the GPU: every request's result equals its result alone."""
+
+import math
+
+import pytest
+
+from paper_1903_03056_gb300 import serve
+
+
+def _small_stream(n, rate, seed=1):
+    return serve.mixed_stream(n, rate, seed=seed, sizes=(8, 12, 16), max_batch=64)
+
+
+def test_stream_is_seeded_and_shaped():
+    a, b = _small_stream(20, 100.0), _small_stream(20, 100.0)
+    assert [(r.N, r.masses, r.batch, r.arrival) for r in a] == [(r.N, r.masses, r.batch, r.arrival) for r in b]
+    assert all(r.N in (8, 12, 16) and r.s in (2, 3) and 1 <= r.batch <= 64 for r in a)
+    assert all(1.0 <= m <= 4.0 for r in a for m in r.masses)
+    assert all(x.arrival <= y.arrival for x, y in zip(a, a[1:]))
+
+
+def test_percentile():
+    assert serve.percentile([1, 2, 3, 4], 50) == 2.5
+    assert serve.percentile(list(range(101)), 99) == 99
+
+
+def test_admission_respects_budget_and_slots():
+    fake = serve.FakeExecutor(seconds_per_node=2e-5, bytes_per_node=1 << 20, plan_bytes=1 << 24)
+    budget = (1 << 24) * 3 + (1 << 20) * 150
+    eng = serve.ServingEngine(fake, budget_bytes=budget, slots=4)
+    reqs = _small_stream(40, math.inf)
+    st = eng.run(reqs)
+    assert st.n == 40 and all(r.done is not None for r in reqs)
+    assert st.peak_bytes <= budget and st.peak_inflight <= 4 and fake.max_active <= 4
+    assert st.peak_inflight > 1
+    assert st.p50 <= st.p99
+
+
+def test_admission_in_arrival_order():
+    fake = serve.FakeExecutor(seconds_per_node=1e-5)
+    eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=3)
+    reqs = _small_stream(30, 2000.0, seed=3)
+    eng.run(reqs)
+    order = [rid for kind, rid, _ in fake.log if kind == "submit"]
+    assert order == sorted(order)
+
+
+def test_request_larger_than_budget_is_an_error():
+    fake = serve.FakeExecutor(bytes_per_node=1 << 30)
+    eng = serve.ServingEngine(fake, budget_bytes=1 << 30, slots=2)
+    with pytest.raises(RuntimeError):
+        eng.run(_small_stream(3, math.inf))
+
+
+@pytest.mark.gpu
+def test_each_result_equals_its_result_alone():
+    import torch
+    from paper_1903_03056_gb300 import build
+    build.build()
+    ex = serve.GpuExecutor(slots=4, keep_outputs=True)
+    reqs = _small_stream(16, 400.0, seed=11)
+    st = serve.ServingEngine(ex, budget_bytes=8 << 30, slots=4).run(reqs)
+    print("serving mix:", st.as_dict())
+    assert st.peak_inflight > 1
+    for r in reqs:
+        alone = ex.run_alone(r)
+        assert torch.equal(ex.outputs[r.rid], alone), r.rid

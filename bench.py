@@ -180,6 +180,23 @@ def reference_arm(args):
 
 # ---- GPU arm ---------------------------------------------------------------------------------
 
+def rank_nodes(rank, batch):
+    """Node indices of one rank: every rank evaluates its own batch (weak scaling)."""
+    return range(rank * batch, (rank + 1) * batch)
+
+
+def aggregate_ranks(ms_local, batch, world, dist=None, device="cpu"):
+    """Max of the ranks' per-step times and the whole-job rate world * batch / max time.
+    The only collective of the path: an all_reduce(MAX) of one number."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * batch / (ms * 1e-3)
+
+
 def time_steps(torch, fn, steps, warmup, stream, dist=None):
     for _ in range(warmup):
         fn()
@@ -193,13 +210,11 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
         fn()
     end.record(stream)
     torch.cuda.synchronize()
-    ms = start.elapsed_time(end)
+    ms = start.elapsed_time(end) / steps
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, _ = aggregate_ranks(ms, 1, dist.get_world_size(), dist, device="cuda")
         dist.barrier()
-    return ms / steps
+    return ms
 
 
 def serving_leg(args):
@@ -251,7 +266,7 @@ def gpu_arm(args):
     # CPU baseline first (spawned pool before heavy GPU work; rank 0, N=1 only)
     cpu = cpu_baseline(w, cores) if (world == 1 and not args.no_cpu_baseline) else None
 
-    f64 = synth.batch_distribution(w)  # [B, s, N, N, N]
+    f64 = synth.batch_distribution(w, nodes=rank_nodes(rank, B))  # [B, s, N, N, N]
     stream = torch.cuda.Stream()
     flops_node = transforms_per_node(w) * flops_per_transform(w.N)
 

@@ -46,7 +46,7 @@ def sinc(x):
     return np.sinc(np.asarray(x) / np.pi)
 
 
-def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=48):
+def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=64):
     """F^{(ij)}(k, rho, sigma) of Eq. GG:
 
         F = rho^2 * int_{S^2} B_ij(rho, sigma . g_hat) exp(-i pi rho c_j k . g_hat / L) dg_hat

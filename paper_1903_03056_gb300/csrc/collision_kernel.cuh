@@ -69,8 +69,8 @@ struct Geo {
   static_assert(N2 % CL == 0, "pencils must split evenly over the cluster");
   static constexpr size_t SMEM = size_t(GP) * NBUF * N * PITCH * sizeof(C<T>);
   // workspace volumes per cluster: f_hat_i, f_hat_j, two double-buffered pairs of shifted
-  // volumes, P, and the two gain accumulators
-  static constexpr int SLOT = 9;
+  // volumes, two P volumes (the second used by the VSS pipeline), two gain accumulators
+  static constexpr int SLOT = 10;
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -164,8 +164,10 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
   CT* const HA1 = scr + 4 * N3;
   CT* const HB1 = scr + 5 * N3;
   CT* const PV = scr + 6 * N3;
-  CT* const QA = scr + 7 * N3;
-  CT* const QB = scr + 8 * N3;
+  CT* const PV1 = scr + 7 * N3;
+  CT* const QA = scr + 8 * N3;
+  CT* const QB = scr + 9 * N3;
+  const bool vss = p.vss != 0;
   const int plane0 = rank * G::PLANES;
   const int pencil0 = rank * G::PENCILS;
   const T inv_n3 = T(1) / T(N3);
@@ -211,7 +213,10 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
 
     // ---- gain: radial nodes, sigma_x groups, entries ----------------------------------------
     // Phase k runs step A of group k (into buffer k&1) and step B of group k-1 (from buffer
-    // (k-1)&1); one cluster barrier per phase, n_grp + 1 phases per radial node.
+    // (k-1)&1); one cluster barrier per phase, n_grp + 1 phases per radial node.  With VSS
+    // every group is one entry whose product is transformed forward on its own: step B of
+    // entry k-1 writes P volume (k-1)&1 and step C of entry k-2 weights P volume (k-2)&1 by
+    // F(k, rho, sigma) in the same phase (n_grp + 2 phases).
     for (int q = 0; q < p.n_rho; ++q) {
       const CT* const phq = phase_ptr<T, N>(p, task, q, 0, 0, 0);
       if (ph_smem) {
@@ -219,7 +224,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
         __syncthreads();
       }
       const CT* const phb = ph_smem ? phs : phq;
-      for (int k = 0; k <= tk.n_grp; ++k) {
+      const int n_phase = tk.n_grp + (vss ? 2 : 1);
+      for (int k = 0; k < n_phase; ++k) {
         if (k < tk.n_grp) {
           const GroupDesc gd = p.groups[tk.grp_off + k];
           CT* const dA = (k & 1) ? HA1 : HA0;
@@ -239,22 +245,24 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
             for (int n = 0; n < N; ++n) st2<T>(dst + n * N2 + pp, v[n]);
           }
         }
-        if (k > 0) {
+        if (k > 0 && k <= tk.n_grp) {
           const int gi = k - 1;
           const GroupDesc gd = p.groups[tk.grp_off + gi];
           const CT* const sA = (gi & 1) ? HA1 : HA0;
           const CT* const sB = (gi & 1) ? HB1 : HB0;
           // step B: (y, z) planes
-          const bool last = gi == tk.n_grp - 1;
+          const bool last = vss || gi == tk.n_grp - 1;
+          const bool fresh = vss || gi == 0;
+          CT* const PVw = (vss && (gi & 1)) ? PV1 : PV;
           for (int xl = grp; xl < G::PLANES; xl += GP) {
             const int x = plane0 + xl;
             CT P[G::PREG ? N : 1];
             if constexpr (G::PREG) {
 #pragma unroll
-              for (int c = 0; c < N; ++c) P[c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+              for (int c = 0; c < N; ++c) P[c] = fresh ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
             } else {
 #pragma unroll
-              for (int c = 0; c < N; ++c) pb[t * PITCH + c] = gi == 0 ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+              for (int c = 0; c < N; ++c) pb[t * PITCH + c] = fresh ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
             }
             for (int e = gd.first; e < gd.first + gd.count; ++e) {
               const T w = T(p.ent_w[tk.ent_off + e]);
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
               rows_to_cols<T, N>(v, tb, t);
               fft_line<T, N, -1>(v);
 #pragma unroll
-              for (int r = 0; r < N; ++r) st2<T>(PV + x * N2 + r * N + t, v[r]);
+              for (int r = 0; r < N; ++r) st2<T>(PVw + x * N2 + r * N + t, v[r]);
             } else {
 #pragma unroll
               for (int c = 0; c < N; ++c) {
@@ -313,8 +321,45 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
             }
           }
         }
+        if (vss && k >= 2) {
+          // step C (VSS) of entry k-2: forward x transform, Q_hat^+ += F(k, rho, sigma) P_hat;
+          // for a halved self pair F(sigma) + F(-sigma), for the reused (j,i) pair F^(ji)(-sigma)
+          const int e = k - 2;
+          const CT* const PVr = (e & 1) ? PV1 : PV;
+          const int m0 = p.ent_m[2 * (tk.ent_off + e)], m1 = p.ent_m[2 * (tk.ent_off + e) + 1];
+          const bool first = q == 0 && e == 0;
+          for (int u = tid; u < G::PENCILS; u += NT) {
+            const int pp = pencil0 + u;
+            CT v[N];
+#pragma unroll
+            for (int n = 0; n < N; ++n) v[n] = ld2<T>(PVr + n * N2 + pp);
+            fft_line<T, N, -1>(v);
+            for (int o = 0; o < 2; ++o) {
+              const int pair = o == 0 ? tk.out0 : tk.out1;
+              if (pair < 0) break;
+              const double2* F0 = p.Fv + ((size_t(pair) * p.n_rho + q) * p.M + (o == 0 ? m0 : m1)) * N3;
+              const double2* F1 = (o == 0 && tk.out1 < 0 && m1 >= 0)
+                                      ? p.Fv + ((size_t(pair) * p.n_rho + q) * p.M + m1) * N3
+                                      : nullptr;
+              CT* acc = o == 0 ? QA : QB;
+#pragma unroll
+              for (int n = 0; n < N; ++n) {
+                double2 fw = __ldg(F0 + n * N2 + pp);
+                if (F1) {
+                  const double2 f1 = __ldg(F1 + n * N2 + pp);
+                  fw.x += f1.x;
+                  fw.y += f1.y;
+                }
+                CT val = cmul<T>(v[n], mk<T>(T(fw.x), T(fw.y)));
+                if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
+                st2<T>(acc + n * N2 + pp, val);
+              }
+            }
+          }
+        }
         cluster_sync<CL>();
       }
+      if (vss) continue;
       // step C: forward transform of P along x, weight, accumulate
       for (int u = tid; u < G::PENCILS; u += NT) {
         const int pp = pencil0 + u;
@@ -451,6 +496,10 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.Gm = pl.d_Gm;
   kp.scratch = pl.d_scratch;
   kp.phase_smem = pl.shape.phase_smem;
+  kp.vss = pl.vss ? 1 : 0;
+  kp.M = pl.M;
+  kp.Fv = pl.d_Fv;
+  kp.ent_m = pl.d_ent_m;
   const int items = batch * kp.n_tasks;
   const int clusters = items < pl.shape.clusters ? items : pl.shape.clusters;
   cudaLaunchConfig_t cfg = {};

@@ -37,8 +37,13 @@ struct KernelParams {
   const void* phase;      // complex: [task][rho][max_ent][role 2][axis 3][N]
   const double* Fw;       // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3
   const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
-  void* scratch;          // complex: [clusters][9][N^3]
+  void* scratch;          // complex: [clusters][SLOT][N^3]
   int phase_smem;         // 1: the task's phase block of the current rho is staged in smem
+  // VSS (alpha != 1): sigma-dependent complex gain weights, one forward transform per entry
+  int vss;
+  int M;
+  const double2* Fv;      // [s*s][n_rho][M][N^3]: w_rho F^(ij)(k, rho, sigma_m) / N^3
+  const int* ent_m;       // [entries][2]: design index of the entry and of its antipode (-1)
 };
 
 // Conservation projection of one self pair (rows = 5) or one stacked cross pair (rows = 6):
@@ -78,7 +83,10 @@ struct Plan {
   std::vector<GroupDesc> groups;
   std::vector<double> ent_w;
   std::vector<int> ent_sigma;   // design index of each entry
+  std::vector<int> ent_m;       // [entries][2] design index and antipode (VSS)
+  std::vector<int> anti;        // antipode of every design direction, -1 if none
   int max_ent = 0;
+  bool vss = false;             // some alpha_ij != 1
 
   std::vector<double> kappa;       // species-sum weights [s*s]
   std::vector<ConsBlock> cons;     // conservation blocks (DGFS_CONSERVE)
@@ -88,6 +96,8 @@ struct Plan {
   double* d_kappa = nullptr;
   void* d_Qfull = nullptr;         // full operators staged for DGFS_SUM_SPECIES
   double* d_Fw = nullptr;
+  double2* d_Fv = nullptr;         // VSS gain weights (complex)
+  int* d_ent_m = nullptr;
   double* d_Gm = nullptr;
   double* d_ent_w = nullptr;
   void* d_phase = nullptr;
@@ -118,8 +128,11 @@ int configure_f64(Plan& p);
 int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 
-// on-device FP64 VHS weight tables on the plan's stream (tables.cu)
+// on-device FP64 weight tables on the plan's stream (tables.cu)
 int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale);
+int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale);
+int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
+                      const int* d_reps, int n_reps, const int* d_anti);
 
 // conservation projection (in place on Q[batch][s][s][N^3]) and species sum (conserve.cu)
 int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st);

@@ -56,6 +56,55 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
   }
 }
 
+// Gauss-Jacobi rule for the weight (1 + t)^beta on [-1, 1] (Golub-Welsch): the nodes are the
+// eigenvalues of the symmetric tridiagonal Jacobi matrix of the weight, found by bisection on
+// its Sturm sequence; the weights are mu_0 / sum_j p_j(x)^2 with p_j the orthonormal
+// polynomials of the weight.
+static void gauss_jacobi(int n, double beta, std::vector<double>& x, std::vector<double>& w) {
+  const double a = 0.0, b = beta;
+  std::vector<double> al(n), be(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double s = 2.0 * i + a + b;
+    al[i] = i == 0 ? (b - a) / (a + b + 2.0) : (b * b - a * a) / (s * (s + 2.0));
+    if (i >= 1) be[i] = 4.0 * i * (i + a) * (i + b) * (i + a + b) / (s * s * (s + 1.0) * (s - 1.0));
+  }
+  const double mu0 = std::pow(2.0, a + b + 1.0) * std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 2.0);
+  auto below = [&](double xv) {  // number of eigenvalues below xv
+    int c = 0;
+    double d = al[0] - xv;
+    if (d < 0) ++c;
+    for (int i = 1; i < n; ++i) {
+      if (d == 0.0) d = 1e-300;
+      d = (al[i] - xv) - be[i] / d;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double lo = -1.0, hi = 1.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-17; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (below(mid) > j) hi = mid; else lo = mid;
+    }
+    const double xv = 0.5 * (lo + hi);
+    double p0 = 1.0, sum = 1.0;
+    if (n > 1) {
+      double p1 = (xv - al[0]) / std::sqrt(be[1]);
+      sum += p1 * p1;
+      for (int i = 1; i < n - 1; ++i) {
+        const double p2 = ((xv - al[i]) * p1 - std::sqrt(be[i]) * p0) / std::sqrt(be[i + 1]);
+        sum += p2 * p2;
+        p0 = p1;
+        p1 = p2;
+      }
+    }
+    x[j] = xv;
+    w[j] = mu0 / sum;
+  }
+}
+
 // Built-in spherical designs with equal weights 4 pi / M: octahedron (M = 6),
 // icosahedron (M = 12), icosahedron and dodecahedron together (M = 32).
 static bool builtin_design(int M, std::vector<double>& s) {
@@ -213,7 +262,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   for (int k = 0; k < s * s; ++k) {
     if (!(p.omega[k] >= 0.5 && p.omega[k] <= 1.0)) return DGFS_ERR_INVALID_ARG;
     if (!(p.alpha[k] >= 1.0 && p.alpha[k] <= 2.0)) return DGFS_ERR_INVALID_ARG;
-    if (p.alpha[k] != 1.0) return DGFS_ERR_UNSUPPORTED;  // VSS gain weights: not in this build
+    if (p.alpha[k] != 1.0) p.vss = true;
   }
   p.kappa.assign(s * s, 1.0);
   if (d->kappa)
@@ -278,6 +327,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     }
     if (anti[m] < 0) antipodal = false;
   }
+  p.anti = antipodal ? anti : std::vector<int>(M, -1);
   auto positive = [&](int m) {
     const double* a = &p.sigma[3 * m];
     for (int dd = 0; dd < 3; ++dd) {
@@ -293,13 +343,16 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   p.groups.clear();
   p.ent_w.clear();
   p.ent_sigma.clear();
+  p.ent_m.clear();
   p.max_ent = 0;
   for (int i = 0; i < s; ++i) {
     for (int j = antipodal ? i : 0; j < s; ++j) {
       std::vector<std::pair<int, double>> ent;
       for (int m = 0; m < M; ++m) {
         if (antipodal && i == j) {
-          if (positive(m)) ent.push_back({m, 2.0 * p.w_sigma[m]});
+          // VHS: p(sigma) = p(-sigma) and F does not depend on sigma -> doubled weight;
+          // VSS: the weight stays and the table adds F(sigma) + F(-sigma)
+          if (positive(m)) ent.push_back({m, (p.vss ? 1.0 : 2.0) * p.w_sigma[m]});
         } else {
           ent.push_back({m, p.w_sigma[m]});
         }
@@ -315,9 +368,11 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
       tk.ent_off = int(p.ent_w.size());
       tk.n_ent = int(ent.size());
       tk.grp_off = int(p.groups.size());
+      // groups share sigma_x (VHS); with VSS every entry needs its own forward transform and
+      // is its own group
       int first = 0;
       for (int e = 1; e <= int(ent.size()); ++e) {
-        if (e == int(ent.size()) ||
+        if (e == int(ent.size()) || p.vss ||
             std::fabs(p.sigma[3 * ent[e].first] - p.sigma[3 * ent[first].first]) > 1e-12) {
           p.groups.push_back({first, e - first});
           first = e;
@@ -327,6 +382,8 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
       for (auto& e : ent) {
         p.ent_w.push_back(e.second);
         p.ent_sigma.push_back(e.first);
+        p.ent_m.push_back(e.first);
+        p.ent_m.push_back(antipodal ? anti[e.first] : -1);
       }
       p.max_ent = std::max(p.max_ent, tk.n_ent);
       p.tasks.push_back(tk);
@@ -380,7 +437,8 @@ int upload_plan(Plan& p) {
         const double rp = std::pow(p.rho[q], 4.0 - 2.0 * om);
         fcoef[2 * (size_t(o) * NR + q)] = p.w_rho[q] * 4.0 * kPi * b * rp / double(N3);
         fcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
-        gcoef[size_t(o) * NR + q] = 16.0 * kPi * kPi * b * p.w_rho[q] * rp;
+        const double al = p.alpha[o];
+        gcoef[size_t(o) * NR + q] = 8.0 * kPi * kPi * std::pow(2.0, al) / al * b * p.w_rho[q] * rp;
       }
     }
   for (int q = 0; q < NR; ++q) gscale[q] = kPi * p.rho[q] / p.L;
@@ -427,18 +485,61 @@ int upload_plan(Plan& p) {
   int rc;
   void *d_fcoef = nullptr, *d_gcoef = nullptr, *d_gscale = nullptr;
   size_t tmp = 0;
-  if ((rc = dalloc(p, (void**)&p.d_Fw, size_t(P) * NR * N3 * sizeof(double)))) return rc;
   if ((rc = dalloc(p, (void**)&p.d_Gm, size_t(P) * N3 * sizeof(double)))) return rc;
-  total += (size_t(P) * NR * N3 + size_t(P) * N3) * sizeof(double);
-  if ((rc = upload(p, fcoef.data(), fcoef.size(), &d_fcoef, tmp))) return rc;
+  total += size_t(P) * N3 * sizeof(double);
   if ((rc = upload(p, gcoef.data(), gcoef.size(), &d_gcoef, tmp))) return rc;
   if ((rc = upload(p, gscale.data(), gscale.size(), &d_gscale, tmp))) return rc;
-  if ((rc = launch_vhs_tables(p, static_cast<double*>(d_fcoef), static_cast<double*>(d_gcoef),
-                              static_cast<double*>(d_gscale))))
-    return rc;
-  cudaFreeAsync(d_fcoef, p.home);
-  cudaFreeAsync(d_gcoef, p.home);
-  cudaFreeAsync(d_gscale, p.home);
+  std::vector<void*> tmps = {d_gcoef, d_gscale};
+  if (!p.vss) {
+    if ((rc = dalloc(p, (void**)&p.d_Fw, size_t(P) * NR * N3 * sizeof(double)))) return rc;
+    total += size_t(P) * NR * N3 * sizeof(double);
+    if ((rc = upload(p, fcoef.data(), fcoef.size(), &d_fcoef, tmp))) return rc;
+    tmps.push_back(d_fcoef);
+    if ((rc = launch_vhs_tables(p, static_cast<double*>(d_fcoef), static_cast<double*>(d_gcoef),
+                                static_cast<double*>(d_gscale))))
+      return rc;
+  } else {
+    // VSS gain weights: prefactor w_q 2 pi b rho^(4-2 omega) / N^3 and the scale of a per
+    // (pair, rho); a 64-point Gauss-Jacobi rule per pair; representatives of antipodal pairs
+    const int n_t = 64;
+    std::vector<double> vcoef(size_t(P) * NR * 2), gj(size_t(P) * 3 * n_t);
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) {
+        const int o = i * s + j;
+        const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
+        for (int q = 0; q < NR; ++q) {
+          vcoef[2 * (size_t(o) * NR + q)] =
+              p.w_rho[q] * 2.0 * kPi * p.b[o] * std::pow(p.rho[q], 4.0 - 2.0 * p.omega[o]) / double(N3);
+          vcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
+        }
+        std::vector<double> tx, tw;
+        gauss_jacobi(n_t, p.alpha[o] - 1.0, tx, tw);
+        for (int k = 0; k < n_t; ++k) {
+          gj[size_t(o) * 3 * n_t + k] = tx[k];
+          gj[size_t(o) * 3 * n_t + n_t + k] = tw[k];
+          gj[size_t(o) * 3 * n_t + 2 * n_t + k] = std::sqrt(std::max(0.0, 1.0 - tx[k] * tx[k]));
+        }
+      }
+    std::vector<int> reps;
+    for (int m = 0; m < p.M; ++m)
+      if (p.anti[m] < 0 || p.anti[m] >= m) reps.push_back(m);
+    void *d_vc = nullptr, *d_gj = nullptr, *d_sg = nullptr, *d_reps = nullptr, *d_anti = nullptr;
+    if ((rc = dalloc(p, (void**)&p.d_Fv, size_t(P) * NR * p.M * N3 * sizeof(double2)))) return rc;
+    total += size_t(P) * NR * p.M * N3 * sizeof(double2);
+    if ((rc = upload(p, vcoef.data(), vcoef.size(), &d_vc, tmp))) return rc;
+    if ((rc = upload(p, gj.data(), gj.size(), &d_gj, tmp))) return rc;
+    if ((rc = upload(p, p.sigma.data(), p.sigma.size(), &d_sg, tmp))) return rc;
+    if ((rc = upload(p, reps.data(), reps.size(), &d_reps, tmp))) return rc;
+    if ((rc = upload(p, p.anti.data(), p.anti.size(), &d_anti, tmp))) return rc;
+    tmps.insert(tmps.end(), {d_vc, d_gj, d_sg, d_reps, d_anti});
+    if ((rc = launch_vss_tables(p, static_cast<double*>(d_vc), static_cast<double*>(d_gj), n_t,
+                                static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()),
+                                static_cast<int*>(d_anti))))
+      return rc;
+    if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale)))) return rc;
+    if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
+  }
+  for (void* t : tmps) cudaFreeAsync(t, p.home);
   if ((rc = upload(p, p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
   if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
   if ((rc = upload(p, p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
@@ -460,8 +561,8 @@ int upload_plan(Plan& p) {
 }
 
 void free_plan(Plan& p) {
-  void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups,
-                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull};
+  void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
+                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -480,6 +581,8 @@ void free_plan(Plan& p) {
   p.d_cons = nullptr;
   p.d_kappa = nullptr;
   p.d_Qfull = nullptr;
+  p.d_Fv = nullptr;
+  p.d_ent_m = nullptr;
 }
 
 }  // namespace dgfs

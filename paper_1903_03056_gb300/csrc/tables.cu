@@ -1,9 +1,14 @@
-// On-device construction of the FP64 VHS weight tables of a plan (the plan's own stream):
-//   Fw[o][q][k] = w_q 4 pi b_o rho_q^(4 - 2 omega_o) / N^3 * sinc(pi rho_q c_j |k| / L)
-//   Gm[o][k]    = sum_q 16 pi^2 b_o w_q rho_q^(4 - 2 omega_o) sinc(pi rho_q |k| / L)
-// (the VHS gain weight F of Eq. GG with the radial weight and the 1/N^3 of the forward
-// transform folded in, and the loss weight on the same radial rule).  The per-(pair, rho)
-// prefactors and sinc scales come from the host; the N^3-sized loops run here.
+// On-device construction of the FP64 weight tables of a plan (the plan's own stream):
+//   VHS  Fw[o][q][k]    = w_q 4 pi b_o rho_q^(4 - 2 omega_o) / N^3 * sinc(pi rho_q c_j |k| / L)
+//   VSS  Fv[o][q][m][k] = w_q 2 pi b_o rho_q^(4 - 2 omega_o) / N^3
+//                         * sum_t w_t exp(-i a t cos th) J0(a sqrt(1 - t^2) sin th),
+//        a = pi rho_q c_j |k| / L, cos th = k_hat . sigma_m, (t, w_t) the Gauss-Jacobi rule of
+//        the weight (1 + t)^(alpha_o - 1)  (the sphere integral of Eq. GG with the azimuth
+//        integrated to J0); F(k, -sigma) = conj F(k, sigma) gives the antipodes
+//   loss Gm[o][k]       = sum_q (8 pi^2 2^alpha / alpha) b_o w_q rho_q^(4 - 2 omega_o) sinc(pi rho_q |k| / L)
+// (the radial weight and the 1/N^3 of the forward transform folded into F).  The per-(pair,
+// rho) prefactors and scales and the quadrature nodes come from the host; the N^3-sized
+// loops run here.
 #include "dgfs_internal.h"
 
 namespace dgfs {
@@ -38,7 +43,59 @@ __global__ void loss_table_kernel(double* __restrict__ Gm, size_t count, int N, 
   }
 }
 
+__global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int M, int N, const double* __restrict__ coef,
+                                 const double* __restrict__ gj, int n_t, const double* __restrict__ sigma,
+                                 const int* __restrict__ reps, int n_reps, const int* __restrict__ anti) {
+  const size_t N3 = size_t(N) * N * N;
+  const size_t count = size_t(P) * NR * n_reps * N3;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < count; idx += size_t(gridDim.x) * blockDim.x) {
+    const size_t n = idx % N3;
+    const int r = int((idx / N3) % n_reps);
+    const size_t oq = idx / (N3 * n_reps);  // o * NR + q
+    const int o = int(oq / NR);
+    const int m = reps[r];
+    const int a_ = int(n / (size_t(N) * N)), b_ = int((n / N) % N), c_ = int(n % N);
+    const double kx = a_ < N / 2 ? a_ : a_ - N, ky = b_ < N / 2 ? b_ : b_ - N, kz = c_ < N / 2 ? c_ : c_ - N;
+    const double kn = sqrt(kx * kx + ky * ky + kz * kz);
+    const double a = coef[2 * oq + 1] * kn;
+    double mu = 0.0;
+    if (kn > 0.0) mu = (kx * sigma[3 * m] + ky * sigma[3 * m + 1] + kz * sigma[3 * m + 2]) / kn;
+    const double smu = sqrt(fmax(0.0, 1.0 - mu * mu));
+    const double* t = gj + size_t(o) * 3 * n_t;  // nodes, weights, sqrt(1 - t^2)
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < n_t; ++k) {
+      double sv, cv;
+      sincos(a * t[k] * mu, &sv, &cv);
+      const double j = t[n_t + k] * j0(a * t[2 * n_t + k] * smu);
+      re += cv * j;
+      im -= sv * j;
+    }
+    const double pref = coef[2 * oq];
+    Fv[(oq * M + m) * N3 + n] = make_double2(pref * re, pref * im);
+    const int am = anti[m];
+    if (am >= 0 && am != m) Fv[(oq * M + am) * N3 + n] = make_double2(pref * re, -pref * im);
+  }
+}
+
 }  // namespace
+
+int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale) {
+  const size_t N3 = size_t(p.N) * p.N * p.N;
+  const size_t nG = size_t(p.s) * p.s * N3;
+  const unsigned blocks = unsigned(nG / 256 + 1 < 4096 ? nG / 256 + 1 : 4096);
+  loss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Gm, nG, p.N, p.N_rho, d_gcoef, d_gscale);
+  return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
+}
+
+int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
+                      const int* d_reps, int n_reps, const int* d_anti) {
+  const size_t N3 = size_t(p.N) * p.N * p.N;
+  const size_t n = size_t(p.s) * p.s * p.N_rho * n_reps * N3;
+  const unsigned blocks = unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536);
+  vss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Fv, p.s * p.s, p.N_rho, p.M, p.N, d_fcoef, d_gj, n_t, d_sigma,
+                                               d_reps, n_reps, d_anti);
+  return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
+}
 
 int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale) {
   const size_t N3 = size_t(p.N) * p.N * p.N;

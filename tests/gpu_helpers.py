@@ -13,12 +13,12 @@ TOL_FP64 = 1e-11
 
 
 def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", sigma=None,
-                  w_sigma=None, b_override=None, R=0.0):
+                  w_sigma=None, b_override=None, R=0.0, alpha=1.0):
     """f: numpy [B, s, N, N, N] float64 -> Q numpy [B, s, s, N, N, N] from libdgfs."""
     import torch
     dt = torch.float32 if precision == "fp32" else torch.float64
-    plan = dgfs.Plan(N, L, masses, omega, M=M, N_rho=N_rho, precision=precision, sigma=sigma,
-                     w_sigma=w_sigma, b_override=b_override, R=R)
+    plan = dgfs.Plan(N, L, masses, omega, alpha=alpha, M=M, N_rho=N_rho, precision=precision,
+                     sigma=sigma, w_sigma=w_sigma, b_override=b_override, R=R)
     fd = torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=dt)
     Q = plan.eval(fd)
     torch.cuda.synchronize()
@@ -29,8 +29,8 @@ def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", si
 
 
 def oracle_collision(f, *, N, L, masses, omega, M=12, N_rho=8, sigma=None, w_sigma=None,
-                     b_override=None, R=None):
-    prob = fs.make_problem(N, L, masses, omega=omega, M=M, N_rho=N_rho, sigma=sigma,
+                     b_override=None, R=None, alpha=1.0):
+    prob = fs.make_problem(N, L, masses, omega=omega, alpha=alpha, M=M, N_rho=N_rho, sigma=sigma,
                            w_sigma=w_sigma, b_override=b_override, R=R)
     return np.stack([fs.collision(fb, prob)[0] for fb in f])
 

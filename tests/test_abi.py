@@ -44,7 +44,7 @@ def _desc(**kw):
     (dict(N=64), dgfs.DGFS_ERR_UNSUPPORTED_N),
     (dict(L=0.0), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(omega=0.3), dgfs.DGFS_ERR_INVALID_ARG),
-    (dict(alpha=1.4), dgfs.DGFS_ERR_UNSUPPORTED),
+    (dict(alpha=2.5), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(M=7), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(N_rho=0), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(masses=[1.0, -2.0]), dgfs.DGFS_ERR_INVALID_ARG),

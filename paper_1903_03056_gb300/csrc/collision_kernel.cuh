@@ -38,10 +38,10 @@ DGFS_SHAPE(float, 4, 1, 4)
 DGFS_SHAPE(float, 6, 1, 6)
 DGFS_SHAPE(float, 8, 1, 8)
 DGFS_SHAPE(float, 12, 1, 12)
-DGFS_SHAPE(float, 16, 1, 16)
+DGFS_SHAPE(float, 16, 1, 8)
 DGFS_SHAPE(float, 24, 2, 12)
-DGFS_SHAPE(float, 32, 4, 8)
-DGFS_SHAPE(float, 48, 4, 3)
+DGFS_SHAPE(float, 32, 2, 4)
+DGFS_SHAPE(float, 48, 2, 4)
 DGFS_SHAPE(double, 4, 1, 4)
 DGFS_SHAPE(double, 6, 1, 6)
 DGFS_SHAPE(double, 8, 1, 8)
@@ -95,37 +95,53 @@ template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __s
 
 
 // Barrier of one plane group.  A group of N threads that divides a warp lives inside one warp
-// and synchronises only that warp, so the plane groups of a CTA run independently; other
-// sizes fall back to the CTA barrier (every group then runs the same control flow).
-template <int N>
+// and synchronises only that warp.  Otherwise SG = lcm(N, 32) / N consecutive groups form a
+// warp-aligned super-group that synchronises on its own named barrier (ids 1, 2, ...), so
+// super-groups run independently; when the groups of a CTA do not split into super-groups
+// the CTA barrier is used (every group then runs the same control flow).
+constexpr int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+
+template <int N, int GP>
+struct GroupSync {
+  static constexpr int LCM = N / gcd_int(N, 32) * 32;
+  static constexpr int SG = LCM / N;  // plane groups per super-group
+  static constexpr bool WARP = N <= 32 && 32 % N == 0;
+  static constexpr bool NAMED = !WARP && GP % SG == 0 && GP / SG <= 15;
+};
+
+template <int N, int GP>
 __device__ __forceinline__ void group_sync() {
-  if constexpr (N <= 32 && 32 % N == 0) {
+  using S = GroupSync<N, GP>;
+  if constexpr (S::WARP) {
     __syncwarp();
+  } else if constexpr (S::NAMED) {
+    const int sg = int(threadIdx.x) / S::LCM;
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + sg), "n"(S::LCM) : "memory");
   } else {
     __syncthreads();
   }
 }
 
 // transpose a plane held as column t (x[r] = V[r][t]) into row t (x[c] = V[t][c]) and back
-template <typename T, int N>
+template <typename T, int N, int GP>
 __device__ __forceinline__ void cols_to_rows(C<T> (&x)[N], C<T>* tb, int t) {
   constexpr int P = N + 1;
 #pragma unroll
   for (int r = 0; r < N; ++r) tb[r * P + t] = x[r];
-  group_sync<N>();
+  group_sync<N, GP>();
 #pragma unroll
   for (int c = 0; c < N; ++c) x[c] = tb[t * P + c];
-  group_sync<N>();
+  group_sync<N, GP>();
 }
-template <typename T, int N>
+template <typename T, int N, int GP>
 __device__ __forceinline__ void rows_to_cols(C<T> (&x)[N], C<T>* tb, int t) {
   constexpr int P = N + 1;
 #pragma unroll
   for (int c = 0; c < N; ++c) tb[t * P + c] = x[c];
-  group_sync<N>();
+  group_sync<N, GP>();
 #pragma unroll
   for (int r = 0; r < N; ++r) x[r] = tb[r * P + t];
-  group_sync<N>();
+  group_sync<N, GP>();
 }
 
 template <typename T, int N>
@@ -189,7 +205,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
 #pragma unroll
         for (int c = 0; c < N; ++c) v[c] = mk<T>(__ldg(src + t * N + c), T(0));
         fft_line<T, N, -1>(v);
-        rows_to_cols<T, N>(v, tb, t);
+        rows_to_cols<T, N, GP>(v, tb, t);
         fft_line<T, N, -1>(v);
         CT* dst = (sp == 0 ? FI : FJ) + size_t(x) * N2;
 #pragma unroll
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
 #pragma unroll
                 for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
                 fft_line<T, N, +1>(v);
-                cols_to_rows<T, N>(v, tb, t);
+                cols_to_rows<T, N, GP>(v, tb, t);
 #pragma unroll
                 for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], phz[c]);
                 fft_line<T, N, +1>(v);
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
                 if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
               }
               fft_line<T, N, -1>(v);
-              rows_to_cols<T, N>(v, tb, t);
+              rows_to_cols<T, N, GP>(v, tb, t);
               fft_line<T, N, -1>(v);
 #pragma unroll
               for (int r = 0; r < N; ++r) st2<T>(PVw + x * N2 + r * N + t, v[r]);
@@ -417,23 +433,23 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
 #pragma unroll
         for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA0 + x * N2 + r * N + t);
         fft_line<T, N, +1>(v);
-        cols_to_rows<T, N>(v, tb, t);
+        cols_to_rows<T, N, GP>(v, tb, t);
         fft_line<T, N, +1>(v);
 #pragma unroll
         for (int c = 0; c < N; ++c) gain[c] = v[c].x;
 #pragma unroll
         for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB0 + x * N2 + r * N + t);
         fft_line<T, N, +1>(v);
-        cols_to_rows<T, N>(v, tb, t);
+        cols_to_rows<T, N, GP>(v, tb, t);
         fft_line<T, N, +1>(v);
         // row t of this plane; stage through shared memory for a coalesced store
         T* rb = reinterpret_cast<T*>(tb);
 #pragma unroll
         for (int c = 0; c < N; ++c) rb[t * PITCH + c] = gain[c] - __ldg(fi + x * N2 + t * N + c) * v[c].x;
-        group_sync<N>();
+        group_sync<N, GP>();
 #pragma unroll
         for (int r = 0; r < N; ++r) Qout[x * N2 + r * N + t] = rb[r * PITCH + t];
-        group_sync<N>();
+        group_sync<N, GP>();
       }
       cluster_sync<CL>();
     }

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(N * N, 1) collision_noalloc_kernel(const __gri
 #pragma unroll
         for (int c = 0; c < N; ++c) v[c] = make_float2(__ldg(src + t * N + c), 0.0f);
         fft_line<T, N, -1>(v);
-        rows_to_cols<T, N>(v, tb, t);
+        rows_to_cols<T, N, GP>(v, tb, t);
         fft_line<T, N, -1>(v);
         CT* dst = (sp == 0 ? FI : FJ) + size_t(x) * N2;
 #pragma unroll
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(N * N, 1) collision_noalloc_kernel(const __gri
 #pragma unroll
             for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
             fft_line<T, N, +1>(v);
-            cols_to_rows<T, N>(v, tb, t);
+            cols_to_rows<T, N, GP>(v, tb, t);
 #pragma unroll
             for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], phz[c]);
             fft_line<T, N, +1>(v);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(N * N, 1) collision_noalloc_kernel(const __gri
         }
         if (last) {
           fft_line<T, N, -1>(P);
-          rows_to_cols<T, N>(P, tb, t);
+          rows_to_cols<T, N, GP>(P, tb, t);
           fft_line<T, N, -1>(P);
 #pragma unroll
           for (int r = 0; r < N; ++r) st2<T>(PV + x * N2 + r * N + t, P[r]);
@@ -259,14 +259,14 @@ __global__ void __launch_bounds__(N * N, 1) collision_noalloc_kernel(const __gri
 #pragma unroll
       for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA + x * N2 + r * N + t);
       fft_line<T, N, +1>(v);
-      cols_to_rows<T, N>(v, tb, t);
+      cols_to_rows<T, N, GP>(v, tb, t);
       fft_line<T, N, +1>(v);
 #pragma unroll
       for (int c = 0; c < N; ++c) gain[c] = v[c].x;
 #pragma unroll
       for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB + x * N2 + r * N + t);
       fft_line<T, N, +1>(v);
-      cols_to_rows<T, N>(v, tb, t);
+      cols_to_rows<T, N, GP>(v, tb, t);
       fft_line<T, N, +1>(v);
       T* rb = reinterpret_cast<T*>(tb);
 #pragma unroll

@@ -31,8 +31,12 @@ def main():
     dt = torch.float32 if a.precision == "fp32" else torch.float64
     fd = torch.from_numpy(f).to(device="cuda", dtype=dt)
     Q = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=dt, device="cuda")
+    import time
+    t0 = time.perf_counter()
     plan = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho,
                      precision=a.precision)
+    plan_s = time.perf_counter() - t0
+    tables, workspace = plan.bytes(0)
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(st)
@@ -42,7 +46,8 @@ def main():
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / a.repeat
     print(json.dumps({"workload": w.name, "batch": B, "precision": a.precision, "ms": ms,
-                      "evals_per_s": B / (ms * 1e-3), "finite": bool(torch.isfinite(Q).all())}))
+                      "evals_per_s": B / (ms * 1e-3), "finite": bool(torch.isfinite(Q).all()),
+                      "plan_s": plan_s, "table_bytes": tables, "workspace_bytes": workspace}))
     plan.close()
 
 

@@ -49,8 +49,14 @@ VSS_N48 = Workload("1024 DG nodes N=48 3-species VSS", 1024, 48, 8.0, (1.0, 1.5,
 HS_N24 = Workload("16384 DG nodes N=24 2-species HS", 16384, 24, 6.0, (1.0, 4.0),
                   0.5, 1.0, 12, 12, "bimaxwellian", 0.0, 4000)
 
+# grids of the serving mix at fixed parameters (tuning and per-size measurements)
+VHS_N16 = Workload("8192 DG nodes N=16 2-species VHS", 8192, 16, 6.0, (1.0, 2.0),
+                   0.75, 1.0, 12, 8, "bimaxwellian", 0.05, 5000)
+VHS_N48 = Workload("512 DG nodes N=48 3-species VHS", 512, 48, 8.0, (1.0, 1.5, 2.6),
+                   0.75, 1.0, 12, 24, "bimaxwellian", 0.05, 6000)
+
 WORKLOADS = {"single_node_n16": SINGLE_NODE_N16, "dg_batch_n32": DG_BATCH_N32,
-             "vss_n48": VSS_N48, "hs_n24": HS_N24}
+             "vss_n48": VSS_N48, "hs_n24": HS_N24, "vhs_n16": VHS_N16, "vhs_n48": VHS_N48}
 
 
 def grid(N, L):

@@ -89,6 +89,16 @@ __device__ __forceinline__ void cluster_sync() {
   }
 }
 
+// read an int in the shared memory of the cluster's rank-0 CTA (distributed shared memory)
+__device__ __forceinline__ int ld_rank0(const int* local) {
+  const unsigned addr = static_cast<unsigned>(__cvta_generic_to_shared(local));
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(remote) : "r"(addr));
+  int v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(remote) : "memory");
+  return v;
+}
+
 // workspace loads/stores go to L2 only: the data is written by other SMs of the cluster
 template <typename T> __device__ __forceinline__ C<T> ld2(const C<T>* p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __stcg(p, v); }
@@ -171,7 +181,6 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
 
   const int rank = CL == 1 ? 0 : int(cluster_rank());
   const int cid = blockIdx.x / CL;
-  const int n_clusters = gridDim.x / CL;
   CT* scr = reinterpret_cast<CT*>(p.scratch) + size_t(cid) * G::SLOT * N3;
   CT* const FI = scr;
   CT* const FJ = scr + N3;
@@ -188,8 +197,17 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
   const int pencil0 = rank * G::PENCILS;
   const T inv_n3 = T(1) / T(N3);
 
+  // Work items (node, task) are taken from a counter: thread 0 of the rank-0 CTA takes the
+  // next item and the cluster reads it from that CTA's shared memory after a cluster barrier,
+  // so clusters that start late (other kernels holding SMs) find no work left instead of
+  // owning a share of it.  The value for the next item is taken after the first barrier of
+  // the current one, when every CTA has read the current value.
+  __shared__ int s_next_item;
   const int n_items = p.batch * p.n_tasks;
-  for (int item = cid; item < n_items; item += n_clusters) {
+  if (rank == 0 && tid == 0) s_next_item = int(atomicAdd(p.work_counter, 1u));
+  cluster_sync<CL>();
+  for (int item = CL == 1 ? s_next_item : ld_rank0(&s_next_item); item < n_items;
+       item = CL == 1 ? s_next_item : ld_rank0(&s_next_item)) {
     const int b = item / p.n_tasks;
     const int task = item % p.n_tasks;
     const TaskDesc tk = p.tasks[task];
@@ -213,6 +231,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
       }
     }
     cluster_sync<CL>();
+    if (rank == 0 && tid == 0) s_next_item = int(atomicAdd(p.work_counter, 1u));
     for (int u = tid; u < nspec * G::PENCILS; u += NT) {
       const int sp = u / G::PENCILS;
       const int pp = pencil0 + u % G::PENCILS;
@@ -454,6 +473,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const 
       cluster_sync<CL>();
     }
   }
+  // no CTA leaves while another may still read its shared memory (the last item index)
+  if constexpr (CL > 1) cluster_sync<CL>();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -512,6 +533,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.Gm = pl.d_Gm;
   kp.scratch = pl.d_scratch;
   kp.phase_smem = pl.shape.phase_smem;
+  kp.work_counter = pl.d_counter;
   kp.vss = pl.vss ? 1 : 0;
   kp.M = pl.M;
   kp.Fv = pl.d_Fv;
@@ -530,6 +552,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (cudaMemsetAsync(pl.d_counter, 0, sizeof(unsigned), st) != cudaSuccess) return DGFS_ERR_CUDA;
   if (cudaLaunchKernelEx(&cfg, collision_kernel<T, N>, kp) != cudaSuccess) return DGFS_ERR_CUDA;
   return DGFS_OK;
 }

@@ -39,6 +39,7 @@ struct KernelParams {
   const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
   void* scratch;          // complex: [clusters][SLOT][N^3]
   int phase_smem;         // 1: the task's phase block of the current rho is staged in smem
+  unsigned* work_counter; // next work item (reset to 0 before every launch)
   // VSS (alpha != 1): sigma-dependent complex gain weights, one forward transform per entry
   int vss;
   int M;
@@ -108,6 +109,7 @@ struct Plan {
   // workspace
   LaunchShape shape;
   void* d_scratch = nullptr;
+  unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel
   size_t scratch_bytes = 0;
   void* d_stage_f = nullptr;
   void* d_stage_Q = nullptr;

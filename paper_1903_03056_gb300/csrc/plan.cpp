@@ -555,6 +555,7 @@ int upload_plan(Plan& p) {
     if ((rc = dalloc(p, &p.d_Qfull, size_t(p.max_batch) * s * s * N3 * real_size(p)))) return rc;
   }
   if ((rc = dalloc(p, &p.d_scratch, p.scratch_bytes))) return rc;
+  if ((rc = dalloc(p, (void**)&p.d_counter, 256))) return rc;
   // the host arrays above must outlive the copies
   if (cudaStreamSynchronize(p.home) != cudaSuccess) return DGFS_ERR_CUDA;
   return DGFS_OK;
@@ -562,7 +563,8 @@ int upload_plan(Plan& p) {
 
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
-                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m};
+                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
+                  p.d_counter};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -583,6 +585,7 @@ void free_plan(Plan& p) {
   p.d_Qfull = nullptr;
   p.d_Fv = nullptr;
   p.d_ent_m = nullptr;
+  p.d_counter = nullptr;
 }
 
 }  // namespace dgfs

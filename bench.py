@@ -224,7 +224,7 @@ def serving_leg(args):
     at 75% of it."""
     from paper_1903_03056_gb300 import serve
     budget = 120 << 30
-    ex = serve.GpuExecutor(slots=8)
+    ex = serve.GpuExecutor(slots=8, sm_share=args.serve_sm_share)
     eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8)
     calib = serve.mixed_stream(args.serve_calib, math.inf, seed=5000)
     st0 = eng.run(calib)
@@ -234,6 +234,7 @@ def serving_leg(args):
     out = st.as_dict()
     out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
                 "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
+                "sm_share": args.serve_sm_share,
                 "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
                        "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
     return out
@@ -356,6 +357,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-calib", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-sm-share", type=float, default=0.5)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -105,9 +105,12 @@ int dgfs_destroy_plan(dgfs_plan plan);
  * batch <= max_batch (else DGFS_ERR_BUDGET), the full operators being staged in the plan. */
 int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batch, void* stream);
 
-/* The same evaluation from host buffers (pinned or pageable): copies f to the device,
- * evaluates, copies Q back and waits for the stream.  batch <= max_batch, else
- * DGFS_ERR_BUDGET.  The plan's staging buffers are allocated at the first call. */
+/* The same evaluation from host buffers (pinned or pageable; pinned lets the copies run
+ * asynchronously): copies f to the device, evaluates, copies Q back and returns when Q is in
+ * host memory.  Batches of 512 nodes or more are split into up to 8 chunks whose input copy,
+ * evaluation (on `stream`) and output copy (on two copy streams the plan owns) overlap.
+ * batch <= max_batch, else DGFS_ERR_BUDGET.  The plan's staging buffers are allocated at the
+ * first call. */
 int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, int batch,
                              void* stream);
 
@@ -117,6 +120,11 @@ int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace
 
 /* The radial truncation R the plan uses (R = 2S from Eq. domain unless given). */
 int dgfs_plan_radius(dgfs_plan plan, double* R);
+
+/* Limit one launch of the persistent collision kernel to a fraction 0 < share <= 1 of the
+ * thread-block clusters the device holds (default 1).  Concurrent evaluations on different
+ * streams then share the SMs instead of queueing behind one another (serving). */
+int dgfs_plan_set_sm_share(dgfs_plan plan, double share);
 
 /* Kernels enqueued by the most recent evaluation on this plan. */
 int dgfs_plan_launches(dgfs_plan plan, int* launches);

@@ -109,13 +109,12 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   DeviceGuard g(p.device);
   if (!g.ok) return DGFS_ERR_CUDA;
   const size_t n3 = size_t(p.N) * p.N * p.N;
-  const size_t fb = size_t(batch) * p.s * n3 * dgfs::real_size(p);
-  const size_t qb = size_t(batch) * output_pairs(p) * n3 * dgfs::real_size(p);
+  const size_t f_node = size_t(p.s) * n3 * dgfs::real_size(p);
+  const size_t q_node = output_pairs(p) * n3 * dgfs::real_size(p);
   if (!p.d_stage_f) {
-    const size_t fmax = size_t(p.max_batch) * p.s * n3 * dgfs::real_size(p);
-    const size_t qmax = size_t(p.max_batch) * output_pairs(p) * n3 * dgfs::real_size(p);
-    if (cudaMallocAsync(&p.d_stage_f, fmax, p.home) != cudaSuccess ||
-        cudaMallocAsync(&p.d_stage_Q, qmax, p.home) != cudaSuccess || cudaStreamSynchronize(p.home) != cudaSuccess) {
+    if (cudaMallocAsync(&p.d_stage_f, size_t(p.max_batch) * f_node, p.home) != cudaSuccess ||
+        cudaMallocAsync(&p.d_stage_Q, size_t(p.max_batch) * q_node, p.home) != cudaSuccess ||
+        cudaStreamSynchronize(p.home) != cudaSuccess) {
       cudaGetLastError();
       if (p.d_stage_f) cudaFreeAsync(p.d_stage_f, p.home);
       if (p.d_stage_Q) cudaFreeAsync(p.d_stage_Q, p.home);
@@ -126,12 +125,54 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
     }
     p.stage_batch = p.max_batch;
   }
+  if (!p.h2d) {
+    bool ok = cudaStreamCreateWithFlags(&p.h2d, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.d2h, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.ev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < dgfs::Plan::kMaxChunks; ++k)
+      ok = cudaEventCreateWithFlags(&p.ev_h2d[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p.ev_done[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return DGFS_ERR_CUDA;
+    }
+  }
+  // chunks of >= 256 nodes: the input copy of chunk k+1 and the output copy of chunk k-1
+  // overlap the evaluation of chunk k (copies on the plan's two copy streams, evaluation on
+  // the caller's stream)
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(p.d_stage_f, f_host, fb, cudaMemcpyHostToDevice, st) != cudaSuccess) return DGFS_ERR_CUDA;
-  const int rc = launch(p, p.d_stage_f, p.d_stage_Q, batch, st);
-  if (rc != DGFS_OK) return rc;
-  if (cudaMemcpyAsync(Q_host, p.d_stage_Q, qb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return DGFS_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return DGFS_ERR_CUDA;
+  int nchunks = batch / 256;
+  nchunks = nchunks < 1 ? 1 : (nchunks > dgfs::Plan::kMaxChunks ? dgfs::Plan::kMaxChunks : nchunks);
+  const int chunk = (batch + nchunks - 1) / nchunks;
+  if (cudaEventRecord(p.ev_start, st) != cudaSuccess || cudaStreamWaitEvent(p.h2d, p.ev_start, 0) != cudaSuccess)
+    return DGFS_ERR_CUDA;
+  int launches = 0;
+  for (int k = 0; k < nchunks; ++k) {
+    const int b0 = k * chunk;
+    const int nb = batch - b0 < chunk ? batch - b0 : chunk;
+    if (nb <= 0) break;
+    char* sf = static_cast<char*>(p.d_stage_f) + size_t(b0) * f_node;
+    char* sq = static_cast<char*>(p.d_stage_Q) + size_t(b0) * q_node;
+    if (cudaMemcpyAsync(sf, static_cast<const char*>(f_host) + size_t(b0) * f_node, size_t(nb) * f_node,
+                        cudaMemcpyHostToDevice, p.h2d) != cudaSuccess ||
+        cudaEventRecord(p.ev_h2d[k], p.h2d) != cudaSuccess || cudaStreamWaitEvent(st, p.ev_h2d[k], 0) != cudaSuccess)
+      return DGFS_ERR_CUDA;
+    const int rc = launch(p, sf, sq, nb, st);
+    if (rc != DGFS_OK) return rc;
+    launches += p.last_launches;
+    if (cudaEventRecord(p.ev_done[k], st) != cudaSuccess || cudaStreamWaitEvent(p.d2h, p.ev_done[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(static_cast<char*>(Q_host) + size_t(b0) * q_node, sq, size_t(nb) * q_node,
+                        cudaMemcpyDeviceToHost, p.d2h) != cudaSuccess)
+      return DGFS_ERR_CUDA;
+  }
+  p.last_launches = launches;
+  if (cudaStreamSynchronize(p.d2h) != cudaSuccess) return DGFS_ERR_CUDA;
+  return DGFS_OK;
+}
+
+int dgfs_plan_set_sm_share(dgfs_plan plan, double share) {
+  if (!plan || !(share > 0.0) || share > 1.0) return DGFS_ERR_INVALID_ARG;
+  plan->plan.shape.share = share;
   return DGFS_OK;
 }
 

@@ -539,7 +539,9 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.Fv = pl.d_Fv;
   kp.ent_m = pl.d_ent_m;
   const int items = batch * kp.n_tasks;
-  const int clusters = items < pl.shape.clusters ? items : pl.shape.clusters;
+  int limit = int(pl.shape.clusters * pl.shape.share);
+  if (limit < 1) limit = 1;
+  const int clusters = items < limit ? items : limit;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

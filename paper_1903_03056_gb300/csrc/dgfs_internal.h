@@ -62,6 +62,7 @@ struct LaunchShape {
   size_t smem = 0;        // dynamic shared memory per CTA
   int phase_smem = 0;     // phases staged in shared memory
   int clusters = 0;       // resident clusters (persistent grid)
+  double share = 1.0;     // fraction of the resident clusters one launch may use
 };
 
 struct Plan {
@@ -115,6 +116,10 @@ struct Plan {
   void* d_stage_Q = nullptr;
   int stage_batch = 0;
   int last_launches = 0;
+  // host-buffer pipeline: copy streams and per-chunk events
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  static constexpr int kMaxChunks = 8;
+  cudaEvent_t ev_h2d[kMaxChunks] = {}, ev_done[kMaxChunks] = {}, ev_start = nullptr;
 };
 
 size_t real_size(const Plan& p);

@@ -576,6 +576,16 @@ void free_plan(Plan& p) {
     cudaEventDestroy(p.last_eval);
     p.last_eval = nullptr;
   }
+  for (int k = 0; k < Plan::kMaxChunks; ++k) {
+    if (p.ev_h2d[k]) cudaEventDestroy(p.ev_h2d[k]);
+    if (p.ev_done[k]) cudaEventDestroy(p.ev_done[k]);
+    p.ev_h2d[k] = p.ev_done[k] = nullptr;
+  }
+  if (p.ev_start) cudaEventDestroy(p.ev_start);
+  if (p.h2d) cudaStreamDestroy(p.h2d);
+  if (p.d2h) cudaStreamDestroy(p.d2h);
+  p.ev_start = nullptr;
+  p.h2d = p.d2h = nullptr;
   p.d_Fw = p.d_Gm = p.d_ent_w = nullptr;
   p.d_phase = p.d_scratch = p.d_stage_f = p.d_stage_Q = nullptr;
   p.d_tasks = nullptr;

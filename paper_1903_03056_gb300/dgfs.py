@@ -31,7 +31,8 @@ DGFS_SUM_SPECIES = 2
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
-           "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc")
+           "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc",
+           "dgfs_plan_set_sm_share")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -70,6 +71,7 @@ def load():
     lib.dgfs_plan_radius.argtypes = [vp, _dptr]
     lib.dgfs_plan_launches.argtypes = [vp, ctypes.POINTER(ci)]
     lib.dgfs_eval_collision_noalloc.argtypes = [ctypes.POINTER(dgfs_plan_desc), vp, vp, ci, vp]
+    lib.dgfs_plan_set_sm_share.argtypes = [vp, ctypes.c_double]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -124,6 +126,10 @@ def dgfs_plan_launches(plan):
 
 def dgfs_strerror(code):
     return load().dgfs_strerror(code).decode()
+
+
+def dgfs_plan_set_sm_share(plan, share):
+    return load().dgfs_plan_set_sm_share(plan, share)
 
 
 def dgfs_eval_collision_noalloc(desc, f_dev, Q_dev, batch, stream):
@@ -211,6 +217,9 @@ class Plan:
         code, n = dgfs_plan_launches(self.handle)
         _check(code, "dgfs_plan_launches")
         return n
+
+    def set_sm_share(self, share):
+        _check(dgfs_plan_set_sm_share(self.handle, float(share)), "dgfs_plan_set_sm_share")
 
     def bytes(self, batch=0):
         code, t, w = dgfs_plan_bytes(self.handle, batch)

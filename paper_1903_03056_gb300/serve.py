@@ -226,9 +226,11 @@ class FakeExecutor:
 
 class GpuExecutor:
     """Drives libdgfs: plans from a cache (shared by requests with equal parameters), one
-    CUDA stream per slot, device-resident inputs tiled from a seeded node pool."""
+    CUDA stream per slot, device-resident inputs tiled from a seeded node pool.  Every kernel
+    is limited to `sm_share` of the SMs so that concurrent slots share the device."""
 
-    def __init__(self, slots=8, precision="fp32", pool_nodes=32, keep_outputs=False, device=0):
+    def __init__(self, slots=8, precision="fp32", pool_nodes=32, keep_outputs=False, device=0,
+                 sm_share=0.5):
         import torch
 
         from . import dgfs, synth
@@ -243,6 +245,7 @@ class GpuExecutor:
         self.plan_users = collections.Counter()
         self.lock = threading.Lock()
         self.keep_outputs = keep_outputs
+        self.sm_share = sm_share
         self.outputs = {}
         self.state = {}
 
@@ -265,6 +268,9 @@ class GpuExecutor:
                 if plan is None:
                     plan = self.dgfs.Plan(r.N, r.L, list(r.masses), r.omega, M=r.M, N_rho=r.N_rho,
                                           precision=self.precision)
+                    # a kernel takes at most this share of the SMs, so requests in other
+                    # slots run beside it instead of queueing behind it
+                    plan.set_sm_share(self.sm_share)
                     self.plans[r.plan_key] = plan
                 self.plan_users[r.plan_key] += 1
             self._pool(r.N, r.s)

@@ -138,3 +138,22 @@ def test_host_buffer_entry_point(precision):
     with pytest.raises(dgfs.DgfsError):
         plan.eval_host(np.zeros((5, 2, 12, 12, 12), dtype=dt), np.zeros((5, 2, 2, 12, 12, 12), dtype=dt))
     plan.close()
+
+
+def test_host_pipeline_chunks_and_sm_share_give_identical_results():
+    """A 700-node host-buffer call runs as 2 overlapped chunks; a plan limited to a quarter of
+    the clusters computes the same bits."""
+    import torch
+    f = _inputs(8, 4.0, (1.0, 2.0), 700, seed=41).astype(np.float32)
+    plan = dgfs.Plan(8, 4.0, [1.0, 2.0], 0.6, M=6, N_rho=3, precision="fp32", max_batch=700)
+    Qh = np.zeros((700, 2, 2, 8, 8, 8), dtype=np.float32)
+    plan.eval_host(np.ascontiguousarray(f), Qh)
+    assert plan.launches() == 2
+    Qd = plan.eval(torch.from_numpy(f).cuda())
+    plan.set_sm_share(0.25)
+    Qs = plan.eval(torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(Qh, Qd.cpu().numpy()) and torch.equal(Qd, Qs)
+    with pytest.raises(dgfs.DgfsError):
+        plan.set_sm_share(0.0)
+    plan.close()

@@ -33,13 +33,20 @@ template <typename T, int N> struct Shape;
   template <> struct Shape<TT, NN> {                                 \
     static constexpr int cluster = CC;                               \
     static constexpr int groups = GG;                                \
+    static constexpr int min_blocks = 1;                             \
+  };
+#define DGFS_SHAPE3(TT, NN, CC, GG, MB)                              \
+  template <> struct Shape<TT, NN> {                                 \
+    static constexpr int cluster = CC;                               \
+    static constexpr int groups = GG;                                \
+    static constexpr int min_blocks = MB;                            \
   };
 DGFS_SHAPE(float, 4, 1, 4)
 DGFS_SHAPE(float, 6, 1, 6)
 DGFS_SHAPE(float, 8, 1, 8)
 DGFS_SHAPE(float, 12, 1, 12)
-DGFS_SHAPE(float, 16, 1, 8)
-DGFS_SHAPE(float, 24, 2, 12)
+DGFS_SHAPE3(float, 16, 1, 8, 3)
+DGFS_SHAPE3(float, 24, 2, 4, 3)
 DGFS_SHAPE(float, 32, 2, 4)
 DGFS_SHAPE(float, 48, 2, 4)
 DGFS_SHAPE(double, 4, 1, 4)
@@ -51,6 +58,7 @@ DGFS_SHAPE(double, 24, 2, 6)
 DGFS_SHAPE(double, 32, 4, 4)
 DGFS_SHAPE(double, 48, 4, 1)
 #undef DGFS_SHAPE
+#undef DGFS_SHAPE3
 
 template <typename T, int N>
 struct Geo {
@@ -62,6 +70,7 @@ struct Geo {
   static constexpr int NBUF = PREG ? 2 : 3;  // smem rows per plane group: T, A, (P)
   static constexpr int CL = Shape<T, N>::cluster;
   static constexpr int GP = Shape<T, N>::groups;
+  static constexpr int MINB = Shape<T, N>::min_blocks;  // CTAs per SM the registers are sized for
   static constexpr int THREADS = GP * N;
   static constexpr int PLANES = N / CL;       // planes per CTA
   static constexpr int PENCILS = N2 / CL;     // pencils per CTA
@@ -162,7 +171,7 @@ __device__ __forceinline__ const C<T>* phase_ptr(const KernelParams& p, int task
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THREADS, 1) collision_kernel(const KernelParams p) {
+__global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision_kernel(const KernelParams p) {
   using G = Geo<T, N>;
   using CT = C<T>;
   constexpr int N2 = G::N2, N3 = G::N3, CL = G::CL, GP = G::GP, NT = G::THREADS;
@@ -484,7 +493,7 @@ int configure_impl(Plan& pl) {
   auto kern = collision_kernel<T, N>;
   // stage the phase block of the current (task, rho) in shared memory when it fits
   const size_t ph_bytes = size_t(pl.max_ent) * 6 * N * sizeof(C<T>);
-  const bool ph_smem = G::SMEM + ph_bytes <= size_t(200) * 1024;
+  const bool ph_smem = G::MINB * (G::SMEM + ph_bytes) <= size_t(200) * 1024;
   const size_t smem = G::SMEM + (ph_smem ? ph_bytes : 0);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return DGFS_ERR_CUDA;

@@ -241,6 +241,22 @@ class Plan:
         self.eval_ptr(f.data_ptr(), Q.data_ptr(), B, stream)
         return Q
 
+    def capture(self, f, Q, stream=None):
+        """Capture one evaluation of device tensors f -> Q into a CUDA graph (torch.cuda.CUDAGraph)
+        that replays the same launches; f and Q must stay allocated while the graph is used."""
+        import torch
+        st = stream if stream is not None else torch.cuda.Stream()
+        B = f.shape[0]
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):  # warm the launch path outside the capture
+            self.eval_ptr(f.data_ptr(), Q.data_ptr(), B, st)
+        torch.cuda.current_stream().wait_stream(st)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            self.eval_ptr(f.data_ptr(), Q.data_ptr(), B, torch.cuda.current_stream())
+        return g
+
     def eval_host(self, f_host, Q_host, stream=None):
         """Host arrays or tensors (contiguous, plan dtype); copies in, evaluates, copies out."""
         fp = f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data

@@ -27,36 +27,16 @@
 
 namespace dgfs {
 
-// compile-time launch shape per (precision, N): cluster size and plane groups per CTA
+// compile-time launch shape per (precision, N): cluster size, plane groups per CTA, CTAs per SM
 template <typename T, int N> struct Shape;
-#define DGFS_SHAPE(TT, NN, CC, GG)                                   \
-  template <> struct Shape<TT, NN> {                                 \
-    static constexpr int cluster = CC;                               \
-    static constexpr int groups = GG;                                \
-    static constexpr int min_blocks = 1;                             \
-  };
 #define DGFS_SHAPE3(TT, NN, CC, GG, MB)                              \
   template <> struct Shape<TT, NN> {                                 \
     static constexpr int cluster = CC;                               \
     static constexpr int groups = GG;                                \
     static constexpr int min_blocks = MB;                            \
   };
-DGFS_SHAPE(float, 4, 1, 4)
-DGFS_SHAPE(float, 6, 1, 6)
-DGFS_SHAPE(float, 8, 1, 8)
-DGFS_SHAPE(float, 12, 1, 12)
-DGFS_SHAPE3(float, 16, 1, 8, 3)
-DGFS_SHAPE3(float, 24, 2, 4, 3)
-DGFS_SHAPE(float, 32, 2, 4)
-DGFS_SHAPE(float, 48, 2, 4)
-DGFS_SHAPE(double, 4, 1, 4)
-DGFS_SHAPE(double, 6, 1, 6)
-DGFS_SHAPE(double, 8, 1, 8)
-DGFS_SHAPE(double, 12, 1, 12)
-DGFS_SHAPE(double, 16, 1, 8)
-DGFS_SHAPE(double, 24, 2, 6)
-DGFS_SHAPE(double, 32, 4, 4)
-DGFS_SHAPE(double, 48, 4, 1)
+#define DGFS_SHAPE(TT, NN, CC, GG) DGFS_SHAPE3(TT, NN, CC, GG, 1)
+#include "tuned_shapes.h"
 #undef DGFS_SHAPE
 #undef DGFS_SHAPE3
 

@@ -18,6 +18,7 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--checksum", action="store_true", help="add the SHA-1 of the output bytes")
     a = ap.parse_args()
 
     import torch
@@ -45,9 +46,13 @@ def main():
     ev1.record(st)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / a.repeat
-    print(json.dumps({"workload": w.name, "batch": B, "precision": a.precision, "ms": ms,
-                      "evals_per_s": B / (ms * 1e-3), "finite": bool(torch.isfinite(Q).all()),
-                      "plan_s": plan_s, "table_bytes": tables, "workspace_bytes": workspace}))
+    out = {"workload": w.name, "batch": B, "precision": a.precision, "ms": ms,
+           "evals_per_s": B / (ms * 1e-3), "finite": bool(torch.isfinite(Q).all()),
+           "plan_s": plan_s, "table_bytes": tables, "workspace_bytes": workspace}
+    if a.checksum:
+        import hashlib
+        out["sha1"] = hashlib.sha1(Q.cpu().numpy().tobytes()).hexdigest()
+    print(json.dumps(out))
     plan.close()
 
 

@@ -1,0 +1,160 @@
+"""Autotuner of the collision kernel's launch shape.
+
+    python -m paper_1903_03056_gb300.tune [--precision fp32] [--sizes 16 24 32 48] [--write]
+
+For every grid size N it builds the kernel once per candidate shape -- thread-block cluster
+size C, plane groups per CTA GP, CTAs per SM the registers are sized for (MB) -- in a
+temporary copy of the sources (only the translation unit of that precision is recompiled and
+linked with the current build's other objects), runs that build on the size's workload,
+checks that its output is bitwise identical to the current build's (a shape changes which
+thread computes a line, never the arithmetic of a line), and keeps the fastest.  With
+--write the winners replace their lines of csrc/tuned_shapes.h and every timing is recorded
+in csrc/tuned_shapes.json; rebuild afterwards.
+"""
+
+import argparse
+import json
+import os
+import re
+import shutil
+import subprocess
+import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+from . import build
+
+PKG = build.PKG
+ROOT = build.ROOT
+CSRC = build.CSRC
+SHAPES_H = os.path.join(CSRC, "tuned_shapes.h")
+SHAPES_JSON = os.path.join(CSRC, "tuned_shapes.json")
+
+WORKLOAD_FOR_N = {16: ("vhs_n16", 8192), 24: ("hs_n24", 16384), 32: ("dg_batch_n32", 4096),
+                  48: ("vhs_n48", 512)}
+CANDIDATES = {
+    16: [(1, 8, 3), (1, 8, 1), (2, 4, 3), (1, 4, 4), (1, 16, 1)],
+    24: [(2, 4, 3), (2, 12, 1), (1, 8, 2), (2, 4, 2)],
+    32: [(2, 4, 1), (4, 4, 1), (1, 8, 1), (2, 8, 1), (2, 2, 2)],
+    48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2)],
+}
+
+
+def valid(N, C, GP, MB, esize):
+    if N % C or (N * N) % C or (N // C) % GP or GP * N > 1024:
+        return False
+    nbuf = 2 if (esize == 8 and N <= 32) or N <= 16 else 3
+    smem = GP * nbuf * N * (N + 1) * esize
+    return MB * smem <= 227 * 1024 and 65536 // (GP * N * MB) >= 64
+
+
+def _ctype(precision):
+    return "float" if precision == "fp32" else "double"
+
+
+def _shape_line(T, N, C, GP, MB):
+    return "DGFS_SHAPE3(%s, %d, %d, %d, %d)" % (T, N, C, GP, MB)
+
+
+def _patch(text, T, N, line):
+    pat = re.compile(r"^DGFS_SHAPE3?\(%s, %d,[^\n]*\)$" % (T, N), re.M)
+    if not pat.search(text):
+        raise RuntimeError("no shape line for %s N=%d" % (T, N))
+    return pat.sub(line, text)
+
+
+def _variant(tmp, precision, N, shape):
+    """Build a variant tree under tmp; returns its root (with the package inside)."""
+    T = _ctype(precision)
+    C, GP, MB = shape
+    root = os.path.join(tmp, "%s_%d_%d_%d_%d" % (precision, N, C, GP, MB))
+    pkg = os.path.join(root, "paper_1903_03056_gb300")
+    os.makedirs(os.path.join(pkg, "_build"))
+    for f in os.listdir(PKG):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(PKG, f), pkg)
+    shutil.copytree(CSRC, os.path.join(pkg, "csrc"))
+    shutil.copytree(os.path.join(ROOT, "include"), os.path.join(root, "include"))
+    h = os.path.join(pkg, "csrc", "tuned_shapes.h")
+    with open(h) as fh:
+        text = fh.read()
+    with open(h, "w") as fh:
+        fh.write(_patch(text, T, N, _shape_line(T, N, C, GP, MB)))
+    tu = "collision_f32" if precision == "fp32" else "collision_f64"
+    obj = os.path.join(pkg, "_build", tu + ".o")
+    cmd = ([build.nvcc()] + build.ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+           "-I" + os.path.join(root, "include"), "-I" + os.path.join(pkg, "csrc"), "-c",
+           os.path.join(pkg, "csrc", tu + ".cu"), "-o", obj])
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    others = [os.path.join(build.BUILD, f) for f in os.listdir(build.BUILD)
+              if f.endswith(".o") and f != tu + ".o"]
+    res = subprocess.run([build.nvcc()] + build.ARCH + ["-shared", "-o", os.path.join(pkg, "libdgfs.so"), obj] + others,
+                         capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    os.utime(os.path.join(pkg, "libdgfs.so"))
+    return root
+
+
+def _time(root, workload, batch, precision):
+    env = dict(os.environ, PYTHONPATH=root + os.pathsep + ROOT)
+    res = subprocess.run([sys.executable, "-m", "paper_1903_03056_gb300.run_case", "--workload", workload,
+                          "--batch", str(batch), "--precision", precision, "--repeat", "3", "--checksum"],
+                         capture_output=True, text=True, cwd=root, env=env)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def tune(precision="fp32", sizes=(16, 24, 32, 48), write=False, jobs=8):
+    build.build()
+    esize = 4 if precision == "fp32" else 8
+    T = _ctype(precision)
+    record = {}
+    if os.path.exists(SHAPES_JSON):
+        with open(SHAPES_JSON) as fh:
+            record = json.load(fh)
+    with open(SHAPES_H) as fh:
+        header = fh.read()
+    with tempfile.TemporaryDirectory(prefix="dgfs_tune_") as tmp:
+        todo = [(N, sh) for N in sizes for sh in CANDIDATES.get(N, []) if valid(N, *sh, esize)]
+        with ThreadPoolExecutor(max_workers=jobs) as ex:
+            roots = dict(zip(todo, ex.map(lambda t: _variant(tmp, precision, t[0], t[1]), todo)))
+        for N in sizes:
+            workload, batch = WORKLOAD_FOR_N[N]
+            ref = _time(ROOT, workload, batch, precision)
+            rows = []
+            for sh in CANDIDATES.get(N, []):
+                if (N, sh) not in roots:
+                    continue
+                r = _time(roots[(N, sh)], workload, batch, precision)
+                rows.append({"cluster": sh[0], "groups": sh[1], "ctas_per_sm": sh[2], "ms": r["ms"],
+                             "identical": r["sha1"] == ref["sha1"]})
+                print("%s N=%d C=%d GP=%d MB=%d: %.2f ms%s" % (precision, N, sh[0], sh[1], sh[2], r["ms"],
+                      "" if rows[-1]["identical"] else "  (output differs: rejected)"), flush=True)
+            ok = [r for r in rows if r["identical"]]
+            if not ok:
+                continue
+            best = min(ok, key=lambda r: r["ms"])
+            record["%s/%d" % (precision, N)] = {"workload": workload, "batch": batch, "current_ms": ref["ms"],
+                                               "best": best, "candidates": rows}
+            header = _patch(header, T, N, _shape_line(T, N, best["cluster"], best["groups"], best["ctas_per_sm"]))
+    if write:
+        with open(SHAPES_H, "w") as fh:
+            fh.write(header)
+        with open(SHAPES_JSON, "w") as fh:
+            json.dump(record, fh, indent=1, sort_keys=True)
+    return record
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--sizes", type=int, nargs="+", default=[16, 24, 32, 48])
+    ap.add_argument("--write", action="store_true")
+    ap.add_argument("--jobs", type=int, default=8)
+    a = ap.parse_args()
+    rec = tune(a.precision, tuple(a.sizes), a.write, a.jobs)
+    print(json.dumps({k: v["best"] for k, v in rec.items()}, indent=1))

@@ -121,6 +121,15 @@ int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace
 /* The radial truncation R the plan uses (R = 2S from Eq. domain unless given). */
 int dgfs_plan_radius(dgfs_plan plan, double* R);
 
+/* One step of the second-order strong-stability-preserving Runge-Kutta scheme (the time
+ * integrator of Sec. 5, used with dt = 0.01 for the Krook-Wu evolution of Sec. 6.1) for the
+ * spatially homogeneous equation d_t f_i = sum_j kappa_ij Q_ij(f_i, f_j), in place on f_dev
+ * [batch][s][N][N][N]:  f1 = f + dt R(f);  f <- (f + f1 + dt R(f1)) / 2, R being the plan's
+ * species-summed operator.  Needs a DGFS_SUM_SPECIES plan (DGFS_CONSERVE applies to each
+ * evaluation if set) and batch <= max_batch; the two work arrays are allocated at the first
+ * call.  Stream-ordered, asynchronous. */
+int dgfs_ssp_rk2_step(dgfs_plan plan, void* f_dev, double dt, int batch, void* stream);
+
 /* Limit one launch of the persistent collision kernel to a fraction 0 < share <= 1 of the
  * thread-block clusters the device holds (default 1).  Concurrent evaluations on different
  * streams then share the SMs instead of queueing behind one another (serving). */

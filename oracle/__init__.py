@@ -20,6 +20,7 @@ fusion or symmetry reuse:
 * ``krook_wu``       -- the Krook-Wu exact solution of the homogeneous binary mixture
                         (Sec. 6.1) and its time derivative.
 * ``moments``        -- macroscopic moments and the conservation residuals of Eq. consv.
+* ``homogeneous``    -- SSP-RK2 time stepping of the homogeneous equation (Secs. 5, 6.1).
 """
 
-from . import quadrature, kernel, fast_spectral, direct, krook_wu, moments  # noqa: F401
+from . import quadrature, kernel, fast_spectral, direct, krook_wu, moments, homogeneous  # noqa: F401

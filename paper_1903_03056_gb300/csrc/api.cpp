@@ -1,4 +1,5 @@
 // extern "C" entry points of libdgfs.so (declared in include/dgfs.h).
+#include <cmath>
 #include <cstdint>
 #include <new>
 
@@ -167,6 +168,39 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   }
   p.last_launches = launches;
   if (cudaStreamSynchronize(p.d2h) != cudaSuccess) return DGFS_ERR_CUDA;
+  return DGFS_OK;
+}
+
+int dgfs_ssp_rk2_step(dgfs_plan plan, void* f_dev, double dt, int batch, void* stream) {
+  if (!plan || batch < 0 || !std::isfinite(dt)) return DGFS_ERR_INVALID_ARG;
+  dgfs::Plan& p = plan->plan;
+  if (!(p.flags & DGFS_SUM_SPECIES)) return DGFS_ERR_INVALID_ARG;
+  if (batch == 0) return DGFS_OK;
+  if (!f_dev || !aligned16(f_dev)) return DGFS_ERR_INVALID_ARG;
+  if (batch > p.max_batch) return DGFS_ERR_BUDGET;
+  DeviceGuard g(p.device);
+  if (!g.ok) return DGFS_ERR_CUDA;
+  const size_t n = size_t(p.max_batch) * p.s * p.N * p.N * p.N;
+  const size_t bytes = n * dgfs::real_size(p);
+  if (!p.d_rk) {
+    if (cudaMallocAsync(&p.d_rk, 2 * bytes, p.home) != cudaSuccess || cudaStreamSynchronize(p.home) != cudaSuccess) {
+      cudaGetLastError();
+      p.d_rk = nullptr;
+      return DGFS_ERR_OOM;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* f1 = p.d_rk;
+  void* r = static_cast<char*>(p.d_rk) + bytes;
+  const size_t cnt = size_t(batch) * p.s * p.N * p.N * p.N;
+  int rc, launches = 0;
+  if ((rc = launch(p, f_dev, r, batch, st)) != DGFS_OK) return rc;
+  launches += p.last_launches;
+  if ((rc = dgfs::launch_rk_stage(p, 1, f_dev, f1, r, dt, cnt, st)) != DGFS_OK) return rc;
+  if ((rc = launch(p, f1, r, batch, st)) != DGFS_OK) return rc;
+  launches += p.last_launches;
+  if ((rc = dgfs::launch_rk_stage(p, 2, f_dev, f1, r, dt, cnt, st)) != DGFS_OK) return rc;
+  p.last_launches = launches + 2;
   return DGFS_OK;
 }
 

@@ -112,6 +112,7 @@ struct Plan {
   void* d_scratch = nullptr;
   unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel
   size_t scratch_bytes = 0;
+  void* d_rk = nullptr;             // SSP-RK2 workspace: f1 and the right-hand side
   void* d_stage_f = nullptr;
   void* d_stage_Q = nullptr;
   int stage_batch = 0;
@@ -140,6 +141,9 @@ int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, con
 int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps, const int* d_anti);
+
+// SSP-RK2 stage combinations (stepper.cu): stage 1 f1 = f + dt r; stage 2 f = (f + f1 + dt r)/2
+int launch_rk_stage(const Plan& p, int stage, void* f, void* f1, const void* r, double dt, size_t n, cudaStream_t st);
 
 // conservation projection (in place on Q[batch][s][s][N^3]) and species sum (conserve.cu)
 int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st);

@@ -564,7 +564,7 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter};
+                  p.d_counter, p.d_rk};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -596,6 +596,7 @@ void free_plan(Plan& p) {
   p.d_Fv = nullptr;
   p.d_ent_m = nullptr;
   p.d_counter = nullptr;
+  p.d_rk = nullptr;
 }
 
 }  // namespace dgfs

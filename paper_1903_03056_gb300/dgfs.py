@@ -32,7 +32,7 @@ DGFS_SUM_SPECIES = 2
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
            "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc",
-           "dgfs_plan_set_sm_share")
+           "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -72,6 +72,7 @@ def load():
     lib.dgfs_plan_launches.argtypes = [vp, ctypes.POINTER(ci)]
     lib.dgfs_eval_collision_noalloc.argtypes = [ctypes.POINTER(dgfs_plan_desc), vp, vp, ci, vp]
     lib.dgfs_plan_set_sm_share.argtypes = [vp, ctypes.c_double]
+    lib.dgfs_ssp_rk2_step.argtypes = [vp, vp, ctypes.c_double, ci, vp]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -126,6 +127,10 @@ def dgfs_plan_launches(plan):
 
 def dgfs_strerror(code):
     return load().dgfs_strerror(code).decode()
+
+
+def dgfs_ssp_rk2_step(plan, f_dev, dt, batch, stream):
+    return load().dgfs_ssp_rk2_step(plan, f_dev, dt, batch, stream)
 
 
 def dgfs_plan_set_sm_share(plan, share):
@@ -217,6 +222,11 @@ class Plan:
         code, n = dgfs_plan_launches(self.handle)
         _check(code, "dgfs_plan_launches")
         return n
+
+    def ssp_rk2_step(self, f, dt, stream=None):
+        """One SSP-RK2 step of d_t f_i = sum_j kappa_ij Q_ij, in place on the CUDA tensor f."""
+        _check(dgfs_ssp_rk2_step(self.handle, f.data_ptr(), float(dt), int(f.shape[0]),
+                                 _stream_handle(stream)), "dgfs_ssp_rk2_step")
 
     def set_sm_share(self, share):
         _check(dgfs_plan_set_sm_share(self.handle, float(share)), "dgfs_plan_set_sm_share")

@@ -366,3 +366,14 @@ def test_species_sum_definition():
     k = np.array([[1.0, 2.0], [3.0, 4.0]])
     S = moments.species_sum(Q, k)
     assert np.allclose(S[0], Q[0, 0] + 2 * Q[0, 1]) and np.allclose(S[1], 3 * Q[1, 0] + 4 * Q[1, 1])
+
+
+# ---------------------------------------------------------------- homogeneous stepping (Secs. 5, 6.1)
+
+def test_ssp_rk2_is_second_order_taylor_on_a_linear_equation():
+    """For d_t f = lam f one step multiplies by 1 + lam dt + (lam dt)^2 / 2 exactly."""
+    from oracle import homogeneous
+    lam, dt = np.array([-0.7, 0.3]), 0.01
+    f = np.array([1.3, -2.0])
+    got = homogeneous.ssp_rk2_step(f, dt, lambda x: lam * x)
+    assert np.allclose(got, f * (1 + lam * dt + 0.5 * (lam * dt) ** 2), rtol=0, atol=1e-15)

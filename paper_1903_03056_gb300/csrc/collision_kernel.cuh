@@ -143,6 +143,33 @@ __device__ __forceinline__ void rows_to_cols(C<T> (&x)[N], C<T>* tb, int t) {
   group_sync<N, GP>();
 }
 
+// Two-pass transform of a plane: the first line pass, the transpose (columns to rows when
+// COLS_FIRST, rows to columns otherwise), an optional per-element phase, the second line pass.
+// For N >= 32 the passes run as a two-trip loop over one copy of the unrolled line transform,
+// which keeps the kernel's instruction footprint small (measured: +3% at N = 32 and 48); the
+// smaller transforms are faster unrolled.
+template <typename T, int N, int GP, int DIR, bool COLS_FIRST>
+__device__ __forceinline__ void plane_pass2(C<T> (&v)[N], C<T>* tb, int t, const C<T>* ph2) {
+  auto between = [&]() {
+    if constexpr (COLS_FIRST) cols_to_rows<T, N, GP>(v, tb, t); else rows_to_cols<T, N, GP>(v, tb, t);
+    if (ph2 != nullptr) {
+#pragma unroll
+      for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], ph2[c]);
+    }
+  };
+  if constexpr (N >= 32) {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) between();
+      fft_line<T, N, DIR>(v);
+    }
+  } else {
+    fft_line<T, N, DIR>(v);
+    between();
+    fft_line<T, N, DIR>(v);
+  }
+}
+
 template <typename T, int N>
 __device__ __forceinline__ const C<T>* phase_ptr(const KernelParams& p, int task, int q, int e,
                                                   int role, int axis) {
@@ -211,9 +238,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         CT v[N];
 #pragma unroll
         for (int c = 0; c < N; ++c) v[c] = mk<T>(__ldg(src + t * N + c), T(0));
-        fft_line<T, N, -1>(v);
-        rows_to_cols<T, N, GP>(v, tb, t);
-        fft_line<T, N, -1>(v);
+        plane_pass2<T, N, GP, -1, false>(v, tb, t, nullptr);
         CT* dst = (sp == 0 ? FI : FJ) + size_t(x) * N2;
 #pragma unroll
         for (int r = 0; r < N; ++r) st2<T>(dst + r * N + t, v[r]);
@@ -297,11 +322,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
                 const CT* phz = phb + ((e * 2 + role) * 3 + 2) * N;
 #pragma unroll
                 for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
-                fft_line<T, N, +1>(v);
-                cols_to_rows<T, N, GP>(v, tb, t);
-#pragma unroll
-                for (int c = 0; c < N; ++c) v[c] = cmul<T>(v[c], phz[c]);
-                fft_line<T, N, +1>(v);
+                plane_pass2<T, N, GP, +1, true>(v, tb, t, phz);
                 if (role == 0) {
 #pragma unroll
                   for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
@@ -330,9 +351,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
               for (int c = 0; c < N; ++c) {
                 if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
               }
-              fft_line<T, N, -1>(v);
-              rows_to_cols<T, N, GP>(v, tb, t);
-              fft_line<T, N, -1>(v);
+              plane_pass2<T, N, GP, -1, false>(v, tb, t, nullptr);
 #pragma unroll
               for (int r = 0; r < N; ++r) st2<T>(PVw + x * N2 + r * N + t, v[r]);
             } else {
@@ -440,16 +459,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         T gain[N];
 #pragma unroll
         for (int r = 0; r < N; ++r) v[r] = ld2<T>(HA0 + x * N2 + r * N + t);
-        fft_line<T, N, +1>(v);
-        cols_to_rows<T, N, GP>(v, tb, t);
-        fft_line<T, N, +1>(v);
+        plane_pass2<T, N, GP, +1, true>(v, tb, t, nullptr);
 #pragma unroll
         for (int c = 0; c < N; ++c) gain[c] = v[c].x;
 #pragma unroll
         for (int r = 0; r < N; ++r) v[r] = ld2<T>(HB0 + x * N2 + r * N + t);
-        fft_line<T, N, +1>(v);
-        cols_to_rows<T, N, GP>(v, tb, t);
-        fft_line<T, N, +1>(v);
+        plane_pass2<T, N, GP, +1, true>(v, tb, t, nullptr);
         // row t of this plane; stage through shared memory for a coalesced store
         T* rb = reinterpret_cast<T*>(tb);
 #pragma unroll

@@ -49,6 +49,32 @@ def flops_per_transform(N):
     return 5.0 * n3 * np.log2(n3)
 
 
+def kernel_sources_sha1():
+    """SHA-1 over the CUDA sources, to tie a stored ncu traffic figure to the kernel it measured."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1903_03056_gb300", "csrc")
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel
+    sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha1") != kernel_sources_sha1():
+        return None
+    return rec.get("bytes_per_launch")
+
+
 def config_dict(w):
     return {"workload": w.name, "batch": w.batch, "N": w.N, "species": w.s,
             "masses": list(w.masses), "omega": w.omega, "alpha": w.alpha, "L": w.L, "M": w.M,
@@ -225,6 +251,7 @@ def serving_leg(args):
     from paper_1903_03056_gb300 import serve
     budget = 120 << 30
     ex = serve.GpuExecutor(slots=8, sm_share=args.serve_sm_share)
+    warm_s = ex.warmup()
     eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8)
     calib = serve.mixed_stream(args.serve_calib, math.inf, seed=5000)
     st0 = eng.run(calib)
@@ -234,7 +261,7 @@ def serving_leg(args):
     out = st.as_dict()
     out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
                 "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
-                "sm_share": args.serve_sm_share,
+                "sm_share": args.serve_sm_share, "warmup_s": warm_s,
                 "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
                        "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
     return out
@@ -329,7 +356,7 @@ def gpu_arm(args):
         achieved = flops_node * B / (ms32 * 1e-3) / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic("collision_kernel<float,32>"),
                 "kernel": "collision_kernel<float,32>",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
                 "flops_per_node": flops_node}

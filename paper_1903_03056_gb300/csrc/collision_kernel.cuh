@@ -57,6 +57,9 @@ struct Geo {
   static_assert(PLANES % GP == 0, "planes must split evenly over plane groups");
   static_assert(N2 % CL == 0, "pencils must split evenly over the cluster");
   static constexpr size_t SMEM = size_t(GP) * NBUF * N * PITCH * sizeof(C<T>);
+  // L2 prefetch of the workspace reads (measured: a gain from N = 24 on, where the clusters'
+  // workspaces together exceed L2; a loss at N = 16); bulk prefetches need whole 16-byte rows
+  static constexpr bool PF = N >= 24 && (PENCILS * sizeof(C<T>)) % 16 == 0;
   // workspace volumes per cluster: f_hat_i, f_hat_j, two double-buffered pairs of shifted
   // volumes, two P volumes (the second used by the VSS pipeline), two gain accumulators
   static constexpr int SLOT = 10;
@@ -91,6 +94,14 @@ __device__ __forceinline__ int ld_rank0(const int* local) {
 // workspace loads/stores go to L2 only: the data is written by other SMs of the cluster
 template <typename T> __device__ __forceinline__ C<T> ld2(const C<T>* p) { return __ldcg(p); }
 template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __stcg(p, v); }
+
+// Hint that [p, p + bytes) (16-byte aligned, a multiple of 16 bytes) is read soon: one bulk
+// prefetch into L2, so the loads that follow meet L2 rather than DRAM latency.  The workspace
+// of all clusters exceeds L2, so a volume written in one phase is partly evicted before it is
+// read in the next.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 
 // Barrier of one plane group.  A group of N threads that divides a warp lives inside one warp
@@ -279,7 +290,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
           const GroupDesc gd = p.groups[tk.grp_off + k];
           CT* const dA = (k & 1) ? HA1 : HA0;
           CT* const dB = (k & 1) ? HB1 : HB0;
-          // step A: x-pencils with the group's shared x phase
+          // step A: x-pencils with the group's shared x phase.  The CTA's pencils of f_hat_i
+          // and f_hat_j are N rows of PENCILS contiguous elements each; prefetch them first.
+          if constexpr (G::PF) {
+            for (int u = tid; u < 2 * N; u += NT)
+              prefetch_l2((u < N ? FI : FJs) + size_t(u % N) * N2 + pencil0, G::PENCILS * sizeof(CT));
+          }
           for (int u = tid; u < 2 * G::PENCILS; u += NT) {
             const int role = u / G::PENCILS;
             const int pp = pencil0 + u % G::PENCILS;
@@ -303,6 +319,9 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
           const bool last = vss || gi == tk.n_grp - 1;
           const bool fresh = vss || gi == 0;
           CT* const PVw = (vss && (gi & 1)) ? PV1 : PV;
+          // each plane is prefetched one (plane, entry, role) read ahead of its use
+          constexpr bool PF = G::PF;
+          if (PF && t == 0) prefetch_l2(sA + size_t(plane0 + grp) * N2, N2 * sizeof(CT));
           for (int xl = grp; xl < G::PLANES; xl += GP) {
             const int x = plane0 + xl;
             CT P[G::PREG ? N : 1];
@@ -320,6 +339,13 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
                 const CT* vol = (role == 0 ? sA : sB) + size_t(x) * N2;
                 const CT* phy = phb + ((e * 2 + role) * 3 + 1) * N;
                 const CT* phz = phb + ((e * 2 + role) * 3 + 2) * N;
+                if (PF && t == 0) {
+                  const CT* nxt = nullptr;
+                  if (role == 0) nxt = sB + size_t(x) * N2;
+                  else if (e + 1 < gd.first + gd.count) nxt = sA + size_t(x) * N2;
+                  else if (xl + GP < G::PLANES) nxt = sA + size_t(x + GP) * N2;
+                  if (nxt != nullptr) prefetch_l2(nxt, N2 * sizeof(CT));
+                }
 #pragma unroll
                 for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
                 plane_pass2<T, N, GP, +1, true>(v, tb, t, phz);

@@ -306,6 +306,23 @@ class GpuExecutor:
                 self.plans.pop(r.plan_key).close()
                 del self.plan_users[r.plan_key]
 
+    def warmup(self, grids=(16, 24, 32, 48), species=(2, 3)):
+        """One small evaluation per (N, s) through the same calls as `submit`, so the first
+        requests of a run do not pay the one-time start-up of the library and of torch's
+        device operators.  Returns the seconds it took."""
+        torch = self.torch
+        t0 = time.perf_counter()
+        for N in grids:
+            for s in species:
+                r = Request(rid=-1, arrival=0.0, N=N, L=L_FOR_N[N], masses=tuple([1.0] * s),
+                            omega=0.75, M=12, N_rho=N // 2, batch=2)
+                self.prepare(r)
+                self.submit(r, 0)
+                self.streams[0].synchronize()
+                self.release(r)
+        torch.cuda.synchronize(self.dev)
+        return time.perf_counter() - t0
+
     def run_alone(self, r):
         """Evaluate one request by itself (fresh plan, default stream); returns Q."""
         torch = self.torch

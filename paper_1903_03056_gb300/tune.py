@@ -35,16 +35,18 @@ WORKLOAD_FOR_N = {16: ("vhs_n16", 8192), 24: ("hs_n24", 16384), 32: ("dg_batch_n
 CANDIDATES = {
     16: [(1, 8, 3), (1, 8, 1), (2, 4, 3), (1, 4, 4), (1, 16, 1)],
     24: [(2, 4, 3), (2, 12, 1), (1, 8, 2), (2, 4, 2)],
-    32: [(2, 4, 1), (4, 4, 1), (1, 8, 1), (2, 8, 1), (2, 2, 2)],
-    48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2)],
+    32: [(2, 4, 1), (4, 4, 1), (1, 8, 1), (2, 8, 1), (2, 2, 2), (4, 2, 1), (8, 2, 1), (8, 4, 1),
+         (4, 8, 1)],
+    48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2), (4, 4, 1), (4, 2, 1), (8, 2, 1)],
 }
 
 
-def valid(N, C, GP, MB, esize):
+def valid(N, C, GP, MB, csize):
+    """Shape constraints of the kernel; csize = bytes of one complex element."""
     if N % C or (N * N) % C or (N // C) % GP or GP * N > 1024:
         return False
-    nbuf = 2 if (esize == 8 and N <= 32) or N <= 16 else 3
-    smem = GP * nbuf * N * (N + 1) * esize
+    nbuf = 2 if (csize == 8 and N <= 32) or N <= 16 else 3
+    smem = GP * nbuf * N * (N + 1) * csize
     return MB * smem <= 227 * 1024 and 65536 // (GP * N * MB) >= 64
 
 
@@ -110,7 +112,7 @@ def _time(root, workload, batch, precision):
 
 def tune(precision="fp32", sizes=(16, 24, 32, 48), write=False, jobs=8):
     build.build()
-    esize = 4 if precision == "fp32" else 8
+    csize = 8 if precision == "fp32" else 16
     T = _ctype(precision)
     record = {}
     if os.path.exists(SHAPES_JSON):
@@ -119,7 +121,7 @@ def tune(precision="fp32", sizes=(16, 24, 32, 48), write=False, jobs=8):
     with open(SHAPES_H) as fh:
         header = fh.read()
     with tempfile.TemporaryDirectory(prefix="dgfs_tune_") as tmp:
-        todo = [(N, sh) for N in sizes for sh in CANDIDATES.get(N, []) if valid(N, *sh, esize)]
+        todo = [(N, sh) for N in sizes for sh in CANDIDATES.get(N, []) if valid(N, *sh, csize)]
         with ThreadPoolExecutor(max_workers=jobs) as ex:
             roots = dict(zip(todo, ex.map(lambda t: _variant(tmp, precision, t[0], t[1]), todo)))
         for N in sizes:

@@ -38,10 +38,17 @@ def workload():
 
 
 def transforms_per_node(w):
-    """Algorithmic 3D transforms per node: s forward (f), P*N_rho*M inverse (antipodal
-    reuse), (s(s+1)/2)*N_rho forward (sigma-summed VHS products), 2P inverse (gain and loss)."""
+    """Algorithmic 3D transforms per node (antipodal design): s forward (f), P*N_rho*M inverse
+    (a(sigma) of (i,j) is b(-sigma) of (j,i)), the forward transforms of the products, 2P
+    inverse (gain and loss).  VHS sums the products over sigma first: s(s+1)/2 forward per
+    radial node; VSS transforms each (rho, sigma) product, M per cross pair and M/2 per self
+    pair (p(sigma) = p(-sigma))."""
     s, P = w.s, w.s * w.s
-    return s + P * w.N_rho * w.M + (s * (s + 1) // 2) * w.N_rho + 2 * P
+    if w.alpha == 1.0:
+        fwd = (s * (s + 1) // 2) * w.N_rho
+    else:
+        fwd = (s * (s - 1) // 2 * w.M + s * (w.M // 2)) * w.N_rho
+    return s + P * w.N_rho * w.M + fwd + 2 * P
 
 
 def flops_per_transform(N):

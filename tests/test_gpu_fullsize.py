@@ -1,6 +1,14 @@
-"""The 4096-node N=32^3 batch in the launch configuration bench.py times: sampled nodes
-(first, second, middle, last) against the oracle one by one, and properties that hold at any
-size (finite output, identical repeat)."""
+"""Full-size batches in the launch configuration that bench.py and run_case time.
+
+* 4096-node N=32^3 batch (the bench workload) and 16384-node N=24^3 hard-sphere batch:
+  sampled nodes (first, second, middle, last) against the oracle one by one, plus finite
+  output.
+* 1024-node N=48^3 three-species VSS batch: the oracle's VSS gain table alone would take
+  tens of minutes per node at this size, so it is checked through properties that hold at
+  any size.  The FP32 batch agrees with the FP64 path on sampled nodes (the FP64 VSS path is
+  pinned to the oracle at small N), and a node evaluated inside the batch is bitwise equal to
+  the same node evaluated alone.
+"""
 
 import numpy as np
 import pytest
@@ -11,42 +19,81 @@ from paper_1903_03056_gb300 import build, dgfs, synth
 
 pytestmark = pytest.mark.gpu
 
-W = synth.WORKLOADS["dg_batch_n32"]
+_INPUTS = {}
 
 
-@pytest.fixture(scope="module")
-def batch_inputs():
-    build.build()
-    dgfs.load()
-    return synth.batch_distribution(W)
+def _inputs(key):
+    if key not in _INPUTS:
+        build.build()
+        dgfs.load()
+        _INPUTS.clear()  # keep one batch in host memory at a time
+        _INPUTS[key] = synth.batch_distribution(synth.WORKLOADS[key])
+    return _INPUTS[key]
 
 
-def _oracle_nodes(f, nodes):
-    prob = fs.make_problem(W.N, W.L, list(W.masses), omega=W.omega, alpha=W.alpha, M=W.M,
-                           N_rho=W.N_rho)
+def _plan(w, precision):
+    return dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho,
+                     precision=precision)
+
+
+def _oracle_nodes(w, f, nodes):
+    prob = fs.make_problem(w.N, w.L, list(w.masses), omega=w.omega, alpha=w.alpha, M=w.M,
+                           N_rho=w.N_rho)
     return np.stack([fs.collision(f[b], prob)[0] for b in nodes])
 
 
-@pytest.mark.parametrize("precision,nodes", [("fp32", [0, 1, 2047, 4095]), ("fp64", [0, 4095])])
-def test_full_batch_sampled_nodes(batch_inputs, precision, nodes):
+def _eval(w, f, precision, nodes=None):
+    """Evaluate the whole batch (nodes=None) or only the listed nodes; returns a torch tensor."""
     import torch
     dt = torch.float32 if precision == "fp32" else torch.float64
-    plan = dgfs.Plan(W.N, W.L, list(W.masses), W.omega, alpha=W.alpha, M=W.M, N_rho=W.N_rho,
-                     precision=precision)
-    fd = torch.from_numpy(batch_inputs).to(device="cuda", dtype=dt)
+    plan = _plan(w, precision)
+    src = f if nodes is None else f[nodes]
+    fd = torch.from_numpy(np.ascontiguousarray(src)).to(device="cuda", dtype=dt)
     Q = plan.eval(fd)
     torch.cuda.synchronize()
+    plan.close()
+    return Q
+
+
+@pytest.mark.parametrize("key,precision,nodes", [
+    ("dg_batch_n32", "fp32", [0, 1, 2047, 4095]),
+    ("dg_batch_n32", "fp64", [0, 4095]),
+    ("hs_n24", "fp32", [0, 1, 8191, 16383]),
+])
+def test_full_batch_sampled_nodes(key, precision, nodes):
+    import torch
+    w = synth.WORKLOADS[key]
+    f = _inputs(key)
+    Q = _eval(w, f, precision)
     assert bool(torch.isfinite(Q).all())
     sample = Q[nodes].double().cpu().numpy()
     del Q
-    ref = _oracle_nodes(batch_inputs, nodes)
+    ref = _oracle_nodes(w, f, nodes)
     if precision == "fp32":
         err_node = max_rel_error(sample, ref, "node")
         err_pair = max_rel_error(sample, ref, "pair")
-        print("fp32 error vs oracle: per node %.3e, per pair %.3e" % (err_node, err_pair))
+        print("%s fp32 error vs oracle: per node %.3e, per pair %.3e" % (key, err_node, err_pair))
         assert err_node < TOL_FP32
     else:
         err = max_rel_error(sample, ref, "pair")
-        print("fp64 error vs oracle: per pair %.3e" % err)
+        print("%s fp64 error vs oracle: per pair %.3e" % (key, err))
         assert err < TOL_FP64
-    plan.close()
+
+
+def test_vss_n48_full_batch_properties():
+    import torch
+    w = synth.WORKLOADS["vss_n48"]
+    f = _inputs("vss_n48")
+    nodes = [0, w.batch - 1]
+    Q = _eval(w, f, "fp32")
+    assert bool(torch.isfinite(Q).all())
+    sample = Q[nodes].cpu()
+    del Q
+    # the same nodes alone: bitwise equal (work items do not interact)
+    alone = _eval(w, f, "fp32", nodes).cpu()
+    assert torch.equal(sample, alone)
+    # against the FP64 path on the same nodes
+    ref = _eval(w, f, "fp64", nodes).cpu().numpy()
+    err = max_rel_error(sample.double().numpy(), ref, "node")
+    print("vss_n48 fp32 vs fp64 path: per node %.3e" % err)
+    assert err < TOL_FP32

@@ -127,7 +127,13 @@ def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
             el = np.exp(1j * np.pi * rho * cj * ks / L)
             em = np.exp(-1j * np.pi * rho * ci * ks / L)
             G += w_rho * w_sig * F[wrap] * el[:, None] * em[None, :]
-    Gm = loss_weight_by_quadrature(K, prob.rho, prob.w_rho, prob.b[i, j], prob.omega[i, j],
+    if prob.loss_rule == "accurate":
+        # 4 N_rho Gauss-Legendre nodes on [0, R] for the loss weight's radial integral
+        x, w = np.polynomial.legendre.leggauss(4 * len(prob.rho))
+        loss_rho, loss_w = 0.5 * prob.R * (x + 1.0), 0.5 * prob.R * w
+    else:
+        loss_rho, loss_w = prob.rho, prob.w_rho
+    Gm = loss_weight_by_quadrature(K, loss_rho, loss_w, prob.b[i, j], prob.omega[i, j],
                                    prob.alpha[i, j], L, n_t, n_phi)
     G -= Gm[None, :]
     terms = alias * G * fh_i[:, None] * fh_j[None, :]

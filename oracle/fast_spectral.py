@@ -50,6 +50,10 @@ class Problem:
     w_rho: np.ndarray             # [N_rho]
     R: float
     extra: dict = field(default_factory=dict)
+    # radial rule of the loss weight G^-: "same" (the gain's N_rho nodes) or "accurate"
+    # (4 N_rho Gauss-Legendre nodes on [0, R]); the paper asks for G^- "to high accuracy"
+    # without naming a rule
+    loss_rule: str = "same"
 
     @property
     def s(self):
@@ -57,7 +61,7 @@ class Problem:
 
 
 def make_problem(N, L, masses, omega, alpha=1.0, M=6, N_rho=None, R=None,
-                 b_override=None, sigma=None, w_sigma=None):
+                 b_override=None, sigma=None, w_sigma=None, loss_rule="same"):
     """Build the discretisation.  ``omega``/``alpha`` may be scalars or [s, s] arrays."""
     masses = np.asarray(masses, dtype=np.float64)
     s = len(masses)
@@ -77,8 +81,11 @@ def make_problem(N, L, masses, omega, alpha=1.0, M=6, N_rho=None, R=None,
     if N_rho is None:
         N_rho = N
     rho, w_rho = quadrature.gauss_legendre_radial(N_rho, R)
+    if loss_rule not in ("same", "accurate"):
+        raise ValueError(loss_rule)
     return Problem(N=N, L=float(L), masses=masses, omega=omega, alpha=alpha, b=b,
-                   sigma=sigma, w_sigma=w_sigma, rho=rho, w_rho=w_rho, R=float(R))
+                   sigma=sigma, w_sigma=w_sigma, rho=rho, w_rho=w_rho, R=float(R),
+                   loss_rule=loss_rule)
 
 
 def velocity_grid(N, L):
@@ -140,10 +147,18 @@ def gain_table(prob, i, j, q, m):
                               prob.omega[i, j], prob.alpha[i, j], prob.L)
 
 
+def loss_rule_nodes(prob):
+    """Radial nodes and weights of the loss weight's rho integral (see Problem.loss_rule)."""
+    if prob.loss_rule == "accurate":
+        return quadrature.gauss_legendre_radial(4 * len(prob.rho), prob.R)
+    return prob.rho, prob.w_rho
+
+
 def loss_table(prob, i, j):
     """G^{(ij)-}(m) on the mode grid."""
     kx, ky, kz = mode_grid(prob.N)
-    return kernel.loss_weight(kx, ky, kz, prob.rho, prob.w_rho, prob.b[i, j],
+    rho, w_rho = loss_rule_nodes(prob)
+    return kernel.loss_weight(kx, ky, kz, rho, w_rho, prob.b[i, j],
                               prob.omega[i, j], prob.alpha[i, j], prob.L)
 
 

@@ -137,8 +137,8 @@ int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st
 int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 
 // on-device FP64 weight tables on the plan's stream (tables.cu)
-int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale);
-int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale);
+int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale, int n_loss);
+int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, int n_loss);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps, const int* d_anti);
 

@@ -245,7 +245,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   if (!(d->L > 0.0) || d->s < 1 || d->s > 8 || !d->mass || !d->omega || !d->alpha) return DGFS_ERR_INVALID_ARG;
   if (d->N_rho < 1 || d->N_rho > 4096 || d->M < 1 || d->max_batch < 0) return DGFS_ERR_INVALID_ARG;
   if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32) return DGFS_ERR_INVALID_ARG;
-  if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES)) != 0u) return DGFS_ERR_INVALID_ARG;
+  if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE)) != 0u) return DGFS_ERR_INVALID_ARG;
   const int s = d->s;
   p.N = d->N;
   p.L = d->L;
@@ -425,23 +425,38 @@ int upload_plan(Plan& p) {
   if (!p.home && cudaStreamCreateWithFlags(&p.home, cudaStreamNonBlocking) != cudaSuccess) return DGFS_ERR_CUDA;
   if (!p.last_eval && cudaEventCreateWithFlags(&p.last_eval, cudaEventDisableTiming) != cudaSuccess)
     return DGFS_ERR_CUDA;
+  // radial rule of the loss weight: the gain's nodes, or (DGFS_LOSS_ACCURATE) 4 N_rho
+  // Gauss-Legendre nodes of its own on [0, R]
+  std::vector<double> lrho = p.rho, lw = p.w_rho;
+  if (p.flags & DGFS_LOSS_ACCURATE) {
+    std::vector<double> x, w;
+    gauss_legendre(4 * NR, x, w);
+    lrho.resize(x.size());
+    lw.resize(x.size());
+    for (size_t q = 0; q < x.size(); ++q) {
+      lrho[q] = 0.5 * p.R * (x[q] + 1.0);
+      lw[q] = 0.5 * p.R * w[q];
+    }
+  }
+  const int NL = int(lrho.size());
   // per (pair, rho) constants of the weight tables: gain prefactor and sinc scale, loss
   // prefactor; the sinc scale of the loss depends on rho only
-  std::vector<double> fcoef(size_t(P) * NR * 2), gcoef(size_t(P) * NR), gscale(NR);
+  std::vector<double> fcoef(size_t(P) * NR * 2), gcoef(size_t(P) * NL), gscale(NL);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
       const int o = i * s + j;
-      const double b = p.b[o], om = p.omega[o];
+      const double b = p.b[o], om = p.omega[o], al = p.alpha[o];
       const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
       for (int q = 0; q < NR; ++q) {
         const double rp = std::pow(p.rho[q], 4.0 - 2.0 * om);
         fcoef[2 * (size_t(o) * NR + q)] = p.w_rho[q] * 4.0 * kPi * b * rp / double(N3);
         fcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
-        const double al = p.alpha[o];
-        gcoef[size_t(o) * NR + q] = 8.0 * kPi * kPi * std::pow(2.0, al) / al * b * p.w_rho[q] * rp;
       }
+      for (int q = 0; q < NL; ++q)
+        gcoef[size_t(o) * NL + q] =
+            8.0 * kPi * kPi * std::pow(2.0, al) / al * b * lw[q] * std::pow(lrho[q], 4.0 - 2.0 * om);
     }
-  for (int q = 0; q < NR; ++q) gscale[q] = kPi * p.rho[q] / p.L;
+  for (int q = 0; q < NL; ++q) gscale[q] = kPi * lrho[q] / p.L;
   // phase factors exp(i pi shift_d k / L) per task, radial node, entry, role, axis
   const int NT = int(p.tasks.size());
   const size_t nph = size_t(NT) * NR * p.max_ent * 2 * 3 * N;
@@ -496,7 +511,7 @@ int upload_plan(Plan& p) {
     if ((rc = upload(p, fcoef.data(), fcoef.size(), &d_fcoef, tmp))) return rc;
     tmps.push_back(d_fcoef);
     if ((rc = launch_vhs_tables(p, static_cast<double*>(d_fcoef), static_cast<double*>(d_gcoef),
-                                static_cast<double*>(d_gscale))))
+                                static_cast<double*>(d_gscale), NL)))
       return rc;
   } else {
     // VSS gain weights: prefactor w_q 2 pi b rho^(4-2 omega) / N^3 and the scale of a per
@@ -536,7 +551,7 @@ int upload_plan(Plan& p) {
                                 static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()),
                                 static_cast<int*>(d_anti))))
       return rc;
-    if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale)))) return rc;
+    if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale), NL))) return rc;
     if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
   }
   for (void* t : tmps) cudaFreeAsync(t, p.home);

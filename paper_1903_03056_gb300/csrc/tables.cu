@@ -79,11 +79,11 @@ __global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int M,
 
 }  // namespace
 
-int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale) {
+int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, int n_loss) {
   const size_t N3 = size_t(p.N) * p.N * p.N;
   const size_t nG = size_t(p.s) * p.s * N3;
   const unsigned blocks = unsigned(nG / 256 + 1 < 4096 ? nG / 256 + 1 : 4096);
-  loss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Gm, nG, p.N, p.N_rho, d_gcoef, d_gscale);
+  loss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Gm, nG, p.N, n_loss, d_gcoef, d_gscale);
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 
@@ -97,12 +97,12 @@ int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 
-int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale) {
+int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale, int n_loss) {
   const size_t N3 = size_t(p.N) * p.N * p.N;
   const size_t nF = size_t(p.s) * p.s * p.N_rho * N3, nG = size_t(p.s) * p.s * N3;
   auto blocks = [](size_t n) { return unsigned(n / 256 + 1 < 4096 ? n / 256 + 1 : 4096); };
   gain_table_kernel<<<blocks(nF), 256, 0, p.home>>>(p.d_Fw, nF, p.N, d_fcoef);
-  loss_table_kernel<<<blocks(nG), 256, 0, p.home>>>(p.d_Gm, nG, p.N, p.N_rho, d_gcoef, d_gscale);
+  loss_table_kernel<<<blocks(nG), 256, 0, p.home>>>(p.d_Gm, nG, p.N, n_loss, d_gcoef, d_gscale);
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 

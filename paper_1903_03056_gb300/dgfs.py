@@ -28,6 +28,7 @@ DGFS_FP64 = 0
 DGFS_FP32 = 1
 DGFS_CONSERVE = 1
 DGFS_SUM_SPECIES = 2
+DGFS_LOSS_ACCURATE = 4
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",

@@ -13,12 +13,12 @@ TOL_FP64 = 1e-11
 
 
 def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", sigma=None,
-                  w_sigma=None, b_override=None, R=0.0, alpha=1.0):
+                  w_sigma=None, b_override=None, R=0.0, alpha=1.0, flags=0):
     """f: numpy [B, s, N, N, N] float64 -> Q numpy [B, s, s, N, N, N] from libdgfs."""
     import torch
     dt = torch.float32 if precision == "fp32" else torch.float64
     plan = dgfs.Plan(N, L, masses, omega, alpha=alpha, M=M, N_rho=N_rho, precision=precision,
-                     sigma=sigma, w_sigma=w_sigma, b_override=b_override, R=R)
+                     sigma=sigma, w_sigma=w_sigma, b_override=b_override, R=R, flags=flags)
     fd = torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=dt)
     Q = plan.eval(fd)
     torch.cuda.synchronize()
@@ -29,9 +29,9 @@ def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", si
 
 
 def oracle_collision(f, *, N, L, masses, omega, M=12, N_rho=8, sigma=None, w_sigma=None,
-                     b_override=None, R=None, alpha=1.0):
+                     b_override=None, R=None, alpha=1.0, loss_rule="same"):
     prob = fs.make_problem(N, L, masses, omega=omega, alpha=alpha, M=M, N_rho=N_rho, sigma=sigma,
-                           w_sigma=w_sigma, b_override=b_override, R=R)
+                           w_sigma=w_sigma, b_override=b_override, R=R, loss_rule=loss_rule)
     return np.stack([fs.collision(fb, prob)[0] for fb in f])
 
 

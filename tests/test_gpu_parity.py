@@ -46,6 +46,21 @@ def test_parity_with_oracle(name, precision):
     assert check(Q, ref, precision)
 
 
+@pytest.mark.parametrize("precision,alpha", [("fp64", 1.0), ("fp32", 1.0), ("fp64", 1.4)])
+def test_parity_accurate_loss_rule(precision, alpha):
+    """DGFS_LOSS_ACCURATE: G^- from its own 4 N_rho-point radial rule, against the oracle's
+    loss_rule="accurate" (VHS and VSS)."""
+    N, L, masses, omega, M, N_rho, B = 12, 5.0, (1.0, 2.6), 0.74, 6, 3, 2
+    f = _inputs(N, L, masses, B, seed=412)
+    kw = dict(N=N, L=L, masses=masses, omega=omega, M=M, N_rho=N_rho, alpha=alpha)
+    Q = gpu_collision(f, precision=precision, flags=dgfs.DGFS_LOSS_ACCURATE, **kw)
+    ref = oracle_collision(f, loss_rule="accurate", **kw)
+    assert check(Q, ref, precision)
+    # the flag changes the result at this coarse radial rule
+    same = oracle_collision(f, **kw)
+    assert np.max(np.abs(ref - same)) > 1e-6 * np.max(np.abs(ref))
+
+
 def test_parity_n48_fp32():
     kw = dict(N=48, L=8.0, masses=(1.0, 2.6), omega=0.74, M=6, N_rho=2)
     f = _inputs(48, 8.0, (1.0, 2.6), 1, seed=148)

@@ -122,6 +122,53 @@ def test_loss_weight_zero_mode_closed_form(omega, alpha):
     assert abs(got[0] / ref - 1) < 1e-11
 
 
+def _loss_radial_by_quad(m, b, omega, alpha, L, R):
+    from scipy.integrate import quad
+    val, _ = quad(lambda r: r ** (4 - 2 * omega) * np.sinc(r * m / L), 0.0, R,
+                  epsabs=0.0, epsrel=1e-13, limit=400)
+    return 8 * np.pi ** 2 * 2 ** alpha / alpha * b * val
+
+
+def test_accurate_loss_rule_matches_adaptive_quadrature():
+    """The accurate loss rule (4 N_rho Gauss-Legendre nodes) against adaptive quadrature of
+    G^-(m) = (8 pi^2 2^alpha / alpha) b int_0^R rho^(4-2 omega) sinc(pi rho |m| / L) drho.
+    Hard spheres (omega = 0.5) give a smooth integrand: agreement to rounding.  omega = 0.74
+    (rho^2.52) converges algebraically: the accurate rule is still the closer of the two."""
+    L, b = 5.0, 0.21
+    for omega, tol in [(0.5, 1e-12), (0.74, None)]:
+        prob_same = fs.make_problem(8, L, [1.0, 2.0], omega=omega, alpha=1.0, N_rho=16)
+        prob_acc = fs.make_problem(8, L, [1.0, 2.0], omega=omega, alpha=1.0, N_rho=16,
+                                   loss_rule="accurate")
+        assert len(fs.loss_rule_nodes(prob_acc)[0]) == 64
+        ms = np.array([0.0, 1.0, 2.0, np.sqrt(3.0) * 4.0])
+        for rule, prob in (("same", prob_same), ("accurate", prob_acc)):
+            rho, w = fs.loss_rule_nodes(prob)
+            got = kernel.loss_weight(ms, 0 * ms, 0 * ms, rho, w, b, omega, 1.0, L)
+            ref = np.array([_loss_radial_by_quad(m, b, omega, 1.0, L, prob.R) for m in ms])
+            err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+            if rule == "same":
+                err_same = err
+            else:
+                err_acc = err
+        if tol is not None:
+            assert err_acc < tol and err_same < tol  # both at rounding for a smooth integrand
+        else:
+            assert err_acc < 0.1 * err_same
+
+
+def test_fast_method_equals_direct_sum_with_accurate_loss_rule():
+    prob = fs.make_problem(4, 5.0, [1.0, 2.0], omega=0.74, alpha=1.0, M=6, N_rho=3,
+                           loss_rule="accurate")
+    f = np.random.default_rng(44).random((2, 4, 4, 4))
+    Qf, _ = fs.collision(f, prob)
+    Qd = direct.collision_direct(f, prob)
+    assert np.max(np.abs(Qf - Qd)) < 1e-12 * np.max(np.abs(Qf))
+    # and the rule changes the result (the loss weight differs at N_rho = 3)
+    Qs, _ = fs.collision(f, fs.make_problem(4, 5.0, [1.0, 2.0], omega=0.74, alpha=1.0, M=6,
+                                            N_rho=3))
+    assert np.max(np.abs(Qf - Qs)) > 1e-6 * np.max(np.abs(Qf))
+
+
 # ---------------------------------------------------------------- Fourier series (Sec. 4)
 
 @pytest.mark.parametrize("N", [4, 6, 8, 12])

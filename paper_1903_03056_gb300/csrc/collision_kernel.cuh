@@ -47,7 +47,6 @@ struct Geo {
   static constexpr int PITCH = N + 1;  // padded smem row (complex elements)
   // P accumulates in registers when a second line of N complex values still fits
   static constexpr bool PREG = (sizeof(T) == 4 && N <= 32) || N <= 16;
-  static constexpr int NBUF = PREG ? 2 : 3;  // smem rows per plane group: T, A, (P)
   static constexpr int CL = Shape<T, N>::cluster;
   static constexpr int GP = Shape<T, N>::groups;
   static constexpr int MINB = Shape<T, N>::min_blocks;  // CTAs per SM the registers are sized for
@@ -56,7 +55,20 @@ struct Geo {
   static constexpr int PENCILS = N2 / CL;     // pencils per CTA
   static_assert(PLANES % GP == 0, "planes must split evenly over plane groups");
   static_assert(N2 % CL == 0, "pencils must split evenly over the cluster");
-  static constexpr size_t SMEM = size_t(GP) * NBUF * N * PITCH * sizeof(C<T>);
+  static constexpr size_t BUF = size_t(N) * PITCH * sizeof(C<T>);  // one padded plane
+  // CTAs an SM holds at once: the register budget's count, or two when a CTA of at most 128
+  // threads (at up to 256 registers each) and two plane buffers per group leave room
+  static constexpr int RES =
+      MINB > 1 ? MINB : (THREADS <= 128 && 2 * (GP * 2 * BUF + 1024) <= 228 * 1024 ? 2 : 1);
+  // y-pass sharing: entries of a group with equal sigma_y reuse the y pass of both shifted
+  // volumes, kept in a transpose buffer per role; needs P in registers and a third buffer per
+  // group that still leaves RES CTAs per SM with 8 KB for the z phases.  Measured on the
+  // 8192-node N = 16 batch: FP32 -4 %, FP64 -11 %; at N = 24 and 32 the third buffer takes
+  // the room of the phase block and of L1 and the kernel ran 5-8 % slower, so it stays off.
+  static constexpr bool YSH = N <= 16 && PREG && RES * (GP * 3 * BUF + 1024 + 8 * 1024) <= 228 * 1024;
+  // smem planes per plane group: transpose (role 0), a, then P (!PREG) or the role-1 transpose
+  static constexpr int NBUF = (PREG && !YSH) ? 2 : 3;
+  static constexpr size_t SMEM = size_t(GP) * NBUF * BUF;
   // L2 prefetch of the workspace reads (measured: a gain from N = 24 on, where the clusters'
   // workspaces together exceed L2; a loss at N = 16); bulk prefetches need whole 16-byte rows
   static constexpr bool PF = N >= 24 && (PENCILS * sizeof(C<T>)) % 16 == 0;
@@ -202,9 +214,13 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
   CT* tb = reinterpret_cast<CT*>(smem_raw) + size_t(grp) * G::NBUF * N * PITCH;
   CT* ab = tb + N * PITCH;
   CT* pb = ab + N * PITCH;  // used only when !PREG
+  CT* const tbB = pb;       // used only when YSH: transpose buffer of role 1
   // phase block of the current (task, rho): [entry][role][axis][N], when staged in smem
   CT* const phs = reinterpret_cast<CT*>(smem_raw) + size_t(GP) * G::NBUF * N * PITCH;
+  // phase block in shared memory: 1 = all axes, 2 = the z phases only (YSH shapes, where the
+  // x and y phases are read once per group or per unshared entry)
   const bool ph_smem = p.phase_smem != 0;
+  const bool ph_zonly = G::YSH && p.phase_smem == 2;
 
   const int rank = CL == 1 ? 0 : int(cluster_rank());
   const int cid = blockIdx.x / CL;
@@ -279,11 +295,14 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
     // F(k, rho, sigma) in the same phase (n_grp + 2 phases).
     for (int q = 0; q < p.n_rho; ++q) {
       const CT* const phq = phase_ptr<T, N>(p, task, q, 0, 0, 0);
-      if (ph_smem) {
+      if (ph_zonly) {
+        for (int u = tid; u < tk.n_ent * 2 * N; u += NT) phs[u] = __ldg(phq + ((u / N) * 3 + 2) * N + u % N);
+        __syncthreads();
+      } else if (ph_smem) {
         for (int u = tid; u < tk.n_ent * 6 * N; u += NT) phs[u] = __ldg(phq + u);
         __syncthreads();
       }
-      const CT* const phb = ph_smem ? phs : phq;
+      const CT* const phb = ph_smem && !ph_zonly ? phs : phq;  // x and y phases
       const int n_phase = tk.n_grp + (vss ? 2 : 1);
       for (int k = 0; k < n_phase; ++k) {
         if (k < tk.n_grp) {
@@ -334,21 +353,58 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             }
             for (int e = gd.first; e < gd.first + gd.count; ++e) {
               const T w = T(p.ent_w[tk.ent_off + e]);
+              // with YSH, an entry whose sigma_y equals the previous entry's in the group reads
+              // the y pass of both volumes back from the role's transpose buffer
+              const bool reuse = G::YSH && e > gd.first && p.ent_ysh[tk.ent_off + e] != 0;
               CT v[N];
               for (int role = 0; role < 2; ++role) {
                 const CT* vol = (role == 0 ? sA : sB) + size_t(x) * N2;
                 const CT* phy = phb + ((e * 2 + role) * 3 + 1) * N;
-                const CT* phz = phb + ((e * 2 + role) * 3 + 2) * N;
-                if (PF && t == 0) {
+                const CT* phz = ph_zonly ? phs + (e * 2 + role) * N : phb + ((e * 2 + role) * 3 + 2) * N;
+                if (PF && t == 0 && !reuse) {
+                  // next plane read: the other role, the next entry that does not reuse, or
+                  // the group's next plane
                   const CT* nxt = nullptr;
-                  if (role == 0) nxt = sB + size_t(x) * N2;
-                  else if (e + 1 < gd.first + gd.count) nxt = sA + size_t(x) * N2;
-                  else if (xl + GP < G::PLANES) nxt = sA + size_t(x + GP) * N2;
+                  if (role == 0) {
+                    nxt = sB + size_t(x) * N2;
+                  } else {
+                    int en = e + 1;
+                    if constexpr (G::YSH) {
+                      while (en < gd.first + gd.count && p.ent_ysh[tk.ent_off + en] != 0) ++en;
+                    }
+                    if (en < gd.first + gd.count) nxt = sA + size_t(x) * N2;
+                    else if (xl + GP < G::PLANES) nxt = sA + size_t(x + GP) * N2;
+                  }
                   if (nxt != nullptr) prefetch_l2(nxt, N2 * sizeof(CT));
                 }
+                if constexpr (G::YSH) {
+                  CT* const yb = role == 0 ? tb : tbB;
+                  constexpr int P_ = PITCH;
+                  if (!reuse) {
 #pragma unroll
-                for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
-                plane_pass2<T, N, GP, +1, true>(v, tb, t, phz);
+                    for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
+                  }
+                  // pass 0: y transform of the column (skipped on reuse); pass 1: z transform
+                  // of row t read back from the role's buffer, with the entry's z phase
+#pragma unroll 1
+                  for (int pass = reuse ? 1 : 0; pass < 2; ++pass) {
+                    if (pass == 1) {
+                      if (!reuse) {
+                        group_sync<N, GP>();  // the previous rows of yb have been read
+#pragma unroll
+                        for (int r = 0; r < N; ++r) yb[r * P_ + t] = v[r];
+                        group_sync<N, GP>();
+                      }
+#pragma unroll
+                      for (int c = 0; c < N; ++c) v[c] = cmul<T>(yb[t * P_ + c], phz[c]);
+                    }
+                    fft_line<T, N, +1>(v);
+                  }
+                } else {
+#pragma unroll
+                  for (int r = 0; r < N; ++r) v[r] = cmul<T>(ld2<T>(vol + r * N + t), phy[r]);
+                  plane_pass2<T, N, GP, +1, true>(v, tb, t, phz);
+                }
                 if (role == 0) {
 #pragma unroll
                   for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
@@ -513,9 +569,18 @@ int configure_impl(Plan& pl) {
   using G = Geo<T, N>;
   auto kern = collision_kernel<T, N>;
   // stage the phase block of the current (task, rho) in shared memory when it fits
+  // (with YSH: only while the SM still holds G::RES CTAs with it)
   const size_t ph_bytes = size_t(pl.max_ent) * 6 * N * sizeof(C<T>);
-  const bool ph_smem = G::MINB * (G::SMEM + ph_bytes) <= size_t(200) * 1024;
-  const size_t smem = G::SMEM + (ph_smem ? ph_bytes : 0);
+  // (with YSH: only while the SM still holds G::RES CTAs with it, else the z phases only)
+  const size_t z_bytes = size_t(pl.max_ent) * 2 * N * sizeof(C<T>);
+  int ph_mode = 0;
+  if (G::YSH) {
+    if (G::RES * (G::SMEM + ph_bytes + 1024) <= size_t(228) * 1024) ph_mode = 1;
+    else if (G::RES * (G::SMEM + z_bytes + 1024) <= size_t(228) * 1024) ph_mode = 2;
+  } else if (G::MINB * (G::SMEM + ph_bytes) <= size_t(200) * 1024) {
+    ph_mode = 1;
+  }
+  const size_t smem = G::SMEM + (ph_mode == 1 ? ph_bytes : ph_mode == 2 ? z_bytes : 0);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
     return DGFS_ERR_CUDA;
   cudaLaunchConfig_t cfg = {};
@@ -538,7 +603,7 @@ int configure_impl(Plan& pl) {
   pl.shape.groups = G::GP;
   pl.shape.threads = G::THREADS;
   pl.shape.smem = smem;
-  pl.shape.phase_smem = ph_smem ? 1 : 0;
+  pl.shape.phase_smem = ph_mode;
   pl.shape.clusters = clusters;
   pl.scratch_bytes = size_t(clusters) * G::SLOT * G::N3 * sizeof(C<T>);
   return DGFS_OK;
@@ -568,6 +633,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.M = pl.M;
   kp.Fv = pl.d_Fv;
   kp.ent_m = pl.d_ent_m;
+  kp.ent_ysh = pl.d_ent_ysh;
   const int items = batch * kp.n_tasks;
   int limit = int(pl.shape.clusters * pl.shape.share);
   if (limit < 1) limit = 1;

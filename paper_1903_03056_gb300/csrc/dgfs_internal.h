@@ -38,13 +38,17 @@ struct KernelParams {
   const double* Fw;       // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3
   const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
   void* scratch;          // complex: [clusters][SLOT][N^3]
-  int phase_smem;         // 1: the task's phase block of the current rho is staged in smem
+  int phase_smem;         // 1: the task's phase block of the current rho is staged in smem;
+                          // 2: only its z phases are
   unsigned* work_counter; // next work item (reset to 0 before every launch)
   // VSS (alpha != 1): sigma-dependent complex gain weights, one forward transform per entry
   int vss;
   int M;
   const double2* Fv;      // [s*s][n_rho][M][N^3]: w_rho F^(ij)(k, rho, sigma_m) / N^3
   const int* ent_m;       // [entries][2]: design index of the entry and of its antipode (-1)
+  const int* ent_ysh;     // [entries]: 1 when the entry has the previous entry's sigma_x and
+                          // sigma_y (same group), so both its shifted volumes share that
+                          // entry's x and y passes
 };
 
 // Conservation projection of one self pair (rows = 5) or one stacked cross pair (rows = 6):
@@ -86,6 +90,7 @@ struct Plan {
   std::vector<double> ent_w;
   std::vector<int> ent_sigma;   // design index of each entry
   std::vector<int> ent_m;       // [entries][2] design index and antipode (VSS)
+  std::vector<int> ent_ysh;     // [entries] shares the previous entry's y pass
   std::vector<int> anti;        // antipode of every design direction, -1 if none
   int max_ent = 0;
   bool vss = false;             // some alpha_ij != 1
@@ -100,6 +105,7 @@ struct Plan {
   double* d_Fw = nullptr;
   double2* d_Fv = nullptr;         // VSS gain weights (complex)
   int* d_ent_m = nullptr;
+  int* d_ent_ysh = nullptr;
   double* d_Gm = nullptr;
   double* d_ent_w = nullptr;
   void* d_phase = nullptr;

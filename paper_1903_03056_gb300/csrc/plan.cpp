@@ -344,6 +344,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   p.ent_w.clear();
   p.ent_sigma.clear();
   p.ent_m.clear();
+  p.ent_ysh.clear();
   p.max_ent = 0;
   for (int i = 0; i < s; ++i) {
     for (int j = antipodal ? i : 0; j < s; ++j) {
@@ -357,8 +358,13 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
           ent.push_back({m, p.w_sigma[m]});
         }
       }
+      // order by sigma_x (groups share the x pass), then by sigma_y (runs of equal sigma_y
+      // inside a group share the y pass as well)
       std::stable_sort(ent.begin(), ent.end(), [&](const std::pair<int, double>& a, const std::pair<int, double>& c) {
-        return p.sigma[3 * a.first] < p.sigma[3 * c.first] - 1e-12;
+        const double* u = &p.sigma[3 * a.first];
+        const double* v = &p.sigma[3 * c.first];
+        if (std::fabs(u[0] - v[0]) > 1e-12) return u[0] < v[0];
+        return u[1] < v[1] - 1e-12;
       });
       TaskDesc tk;
       tk.i = i;
@@ -379,11 +385,19 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
         }
       }
       tk.n_grp = int(p.groups.size()) - tk.grp_off;
-      for (auto& e : ent) {
+      for (size_t k = 0; k < ent.size(); ++k) {
+        const auto& e = ent[k];
         p.ent_w.push_back(e.second);
         p.ent_sigma.push_back(e.first);
         p.ent_m.push_back(e.first);
         p.ent_m.push_back(antipodal ? anti[e.first] : -1);
+        bool ysh = false;
+        if (k > 0 && !p.vss) {
+          const double* u = &p.sigma[3 * ent[k - 1].first];
+          const double* v = &p.sigma[3 * e.first];
+          ysh = std::fabs(u[0] - v[0]) <= 1e-12 && std::fabs(u[1] - v[1]) <= 1e-12;
+        }
+        p.ent_ysh.push_back(ysh ? 1 : 0);
       }
       p.max_ent = std::max(p.max_ent, tk.n_ent);
       p.tasks.push_back(tk);
@@ -558,6 +572,7 @@ int upload_plan(Plan& p) {
   if ((rc = upload(p, p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
   if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
   if ((rc = upload(p, p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
+  if ((rc = upload(p, p.ent_ysh.data(), p.ent_ysh.size(), (void**)&p.d_ent_ysh, total))) return rc;
   if (p.precision == DGFS_FP32) {
     if ((rc = upload(p, phf.data(), phf.size(), &p.d_phase, total))) return rc;
   } else {
@@ -579,7 +594,7 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter, p.d_rk};
+                  p.d_counter, p.d_rk,      p.d_ent_ysh};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -610,6 +625,7 @@ void free_plan(Plan& p) {
   p.d_Qfull = nullptr;
   p.d_Fv = nullptr;
   p.d_ent_m = nullptr;
+  p.d_ent_ysh = nullptr;
   p.d_counter = nullptr;
   p.d_rk = nullptr;
 }

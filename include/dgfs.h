@@ -170,6 +170,61 @@ const char* dgfs_strerror(int code);
 int dgfs_eval_collision_noalloc(const dgfs_plan_desc* desc, const void* f_dev, void* Q_dev,
                                 int batch, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * One-dimensional nodal DG in physical space (Sec. 5): the spatially inhomogeneous equation
+ * d_t f_i + v_x d_x f_i = sum_j kappa_ij Q_ij(f_i, f_j) (Eq. NMBE, kappa_ij = 1/Kn_ij) on
+ * [x0, x1], split into Ne equal elements, each carrying K Gauss-Lobatto-Legendre nodes with
+ * the Lagrange basis on them.  As in Sec. 5 the mass matrix and the collision tensor are taken
+ * with the GLL rule, so both are diagonal and the collision term is the species-summed
+ * operator at every node; the stiffness matrix is exact; the face flux is upwind; the time
+ * step is SSP-RK2.  Walls take the Maxwell boundary condition of Sec. 2, with the wall
+ * density n_w from zero net mass flux through the wall, evaluated as sums over the
+ * velocity grid.
+ *
+ * State layout: f[Ne][K][s][N][N][N] (element, node, species, velocity grid as for
+ * dgfs_eval_collision), i.e. batch = Ne * K collision nodes, element type of the collision
+ * plan's precision, device memory, 16-byte aligned, owned by the caller.  Node positions come
+ * from dgfs_dg_nodes. */
+typedef struct dgfs_dg_plan_s* dgfs_dg_plan; /* opaque, owned by the library */
+
+#define DGFS_BC_PERIODIC 0 /* f(x1) continues at x0 */
+#define DGFS_BC_WALLS 1    /* Maxwell walls at x0 (outward normal -x) and x1 (+x) */
+
+typedef struct {
+  int Ne;          /* elements, >= 1 */
+  int K;           /* GLL nodes per element, 2..8 */
+  double x0, x1;   /* physical domain, x0 < x1 */
+  int bc;          /* DGFS_BC_PERIODIC or DGFS_BC_WALLS */
+  double Tw[2];    /* wall temperatures (left, right), > 0; DGFS_BC_WALLS only */
+  double uw[6];    /* wall velocities (left x, y, z, right x, y, z); the x components are 0 */
+  double acc[2];   /* accommodation coefficients in [0, 1]: 1 diffuse, 0 specular */
+} dgfs_dg_desc;
+
+/* Build a DG plan on top of a collision plan, which supplies the velocity grid (N, L),
+ * the species and masses, the precision and the collision operator; the collision plan must
+ * stay alive while the DG plan is used.  Allocates the step's work buffers on the collision
+ * plan's device (2 * Ne * K * s * N^3 elements).  Errors: DGFS_ERR_INVALID_ARG (null or
+ * out-of-range fields, s > 8), DGFS_ERR_OOM, DGFS_ERR_CUDA. */
+int dgfs_dg_create(const dgfs_dg_desc* desc, dgfs_plan collision, dgfs_dg_plan* out);
+
+/* Release a DG plan (waits for its work).  Null is accepted. */
+int dgfs_dg_destroy(dgfs_dg_plan plan);
+
+/* Physical positions of the Ne * K nodes (host array, element-major). */
+int dgfs_dg_nodes(dgfs_dg_plan plan, double* x_out);
+
+/* rhs = the transport part of d_t f (Eq. weakForm without its collision term): for every
+ * element, node m and velocity, (2 / (h w_m)) [v_x sum_l S_ml f_l - flux terms of the faces].
+ * f_dev and rhs_dev as described above; stream-ordered, asynchronous. */
+int dgfs_dg_transport(dgfs_dg_plan plan, const void* f_dev, void* rhs_dev, void* stream);
+
+/* One SSP-RK2 step of the full equation in place on f_dev:
+ *   f1 = f + dt R(f),  f <- f/2 + (f1 + dt R(f1))/2,
+ * R = transport + sum_j kappa_ij Q_ij, the collision term from the collision plan.  The
+ * collision plan must have been created with DGFS_SUM_SPECIES (its kappa gives 1/Kn_ij) and
+ * max_batch >= Ne * K, else DGFS_ERR_INVALID_ARG / DGFS_ERR_BUDGET.  Stream-ordered. */
+int dgfs_dg_step(dgfs_dg_plan plan, void* f_dev, double dt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,8 @@ fusion or symmetry reuse:
                         (Sec. 6.1) and its time derivative.
 * ``moments``        -- macroscopic moments and the conservation residuals of Eq. consv.
 * ``homogeneous``    -- SSP-RK2 time stepping of the homogeneous equation (Secs. 5, 6.1).
+* ``dg1d``           -- nodal DG in one space dimension (Sec. 5): GLL rule, element matrices,
+                        upwind transport, Maxwell walls (Sec. 2), the RKDG step.
 """
 
-from . import quadrature, kernel, fast_spectral, direct, krook_wu, moments, homogeneous  # noqa: F401
+from . import quadrature, kernel, fast_spectral, direct, krook_wu, moments, homogeneous, dg1d  # noqa: F401

@@ -5,10 +5,6 @@
 
 #include "dgfs_internal.h"
 
-struct dgfs_plan_s {
-  dgfs::Plan plan;
-};
-
 namespace {
 
 // make the plan's device current for the duration of a call

@@ -156,3 +156,8 @@ int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st);
 int launch_species_sum(const Plan& p, const void* Qfull, void* Qsum, int batch, cudaStream_t st);
 
 }  // namespace dgfs
+
+// the opaque plan handle of the C ABI
+struct dgfs_plan_s {
+  dgfs::Plan plan;
+};

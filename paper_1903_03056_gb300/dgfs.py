@@ -29,11 +29,14 @@ DGFS_FP32 = 1
 DGFS_CONSERVE = 1
 DGFS_SUM_SPECIES = 2
 DGFS_LOSS_ACCURATE = 4
+DGFS_BC_PERIODIC = 0
+DGFS_BC_WALLS = 1
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
            "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc",
-           "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step")
+           "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step", "dgfs_dg_create", "dgfs_dg_destroy",
+           "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -50,6 +53,12 @@ class DgfsError(RuntimeError):
     def __init__(self, code, where):
         super().__init__("%s failed: %s (%d)" % (where, dgfs_strerror(code), code))
         self.code = code
+
+
+class dgfs_dg_desc(ctypes.Structure):
+    _fields_ = [("Ne", ctypes.c_int), ("K", ctypes.c_int), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("bc", ctypes.c_int), ("Tw", ctypes.c_double * 2),
+                ("uw", ctypes.c_double * 6), ("acc", ctypes.c_double * 2)]
 
 
 _lib = None
@@ -74,6 +83,11 @@ def load():
     lib.dgfs_eval_collision_noalloc.argtypes = [ctypes.POINTER(dgfs_plan_desc), vp, vp, ci, vp]
     lib.dgfs_plan_set_sm_share.argtypes = [vp, ctypes.c_double]
     lib.dgfs_ssp_rk2_step.argtypes = [vp, vp, ctypes.c_double, ci, vp]
+    lib.dgfs_dg_create.argtypes = [ctypes.POINTER(dgfs_dg_desc), vp, ctypes.POINTER(vp)]
+    lib.dgfs_dg_destroy.argtypes = [vp]
+    lib.dgfs_dg_nodes.argtypes = [vp, _dptr]
+    lib.dgfs_dg_transport.argtypes = [vp, vp, vp, vp]
+    lib.dgfs_dg_step.argtypes = [vp, vp, ctypes.c_double, vp]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -136,6 +150,30 @@ def dgfs_ssp_rk2_step(plan, f_dev, dt, batch, stream):
 
 def dgfs_plan_set_sm_share(plan, share):
     return load().dgfs_plan_set_sm_share(plan, share)
+
+
+def dgfs_dg_create(desc, collision_plan):
+    h = ctypes.c_void_p()
+    code = load().dgfs_dg_create(ctypes.byref(desc), collision_plan, ctypes.byref(h))
+    return code, h.value
+
+
+def dgfs_dg_destroy(plan):
+    return load().dgfs_dg_destroy(plan)
+
+
+def dgfs_dg_nodes(plan, n):
+    x = np.zeros(n)
+    code = load().dgfs_dg_nodes(plan, x.ctypes.data_as(_dptr))
+    return code, x
+
+
+def dgfs_dg_transport(plan, f_dev, rhs_dev, stream):
+    return load().dgfs_dg_transport(plan, f_dev, rhs_dev, stream)
+
+
+def dgfs_dg_step(plan, f_dev, dt, stream):
+    return load().dgfs_dg_step(plan, f_dev, dt, stream)
 
 
 def dgfs_eval_collision_noalloc(desc, f_dev, Q_dev, batch, stream):
@@ -279,6 +317,54 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             dgfs_destroy_plan(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DGPlan:
+    """Owns one 1D DG plan built on a collision ``Plan`` (which must outlive it)."""
+
+    def __init__(self, collision, Ne, K, x0=0.0, x1=1.0, bc="periodic", Tw=(1.0, 1.0),
+                 uw=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), acc=(1.0, 1.0)):
+        d = dgfs_dg_desc()
+        d.Ne, d.K, d.x0, d.x1 = int(Ne), int(K), float(x0), float(x1)
+        d.bc = DGFS_BC_WALLS if bc == "walls" else DGFS_BC_PERIODIC
+        d.Tw[0], d.Tw[1] = float(Tw[0]), float(Tw[1])
+        for k, u in enumerate(np.asarray(uw, dtype=np.float64).reshape(-1)):
+            d.uw[k] = float(u)
+        d.acc[0], d.acc[1] = float(acc[0]), float(acc[1])
+        code, h = dgfs_dg_create(d, collision.handle)
+        _check(code, "dgfs_dg_create")
+        self.handle, self.collision = h, collision
+        self.Ne, self.K = int(Ne), int(K)
+
+    def nodes(self):
+        code, x = dgfs_dg_nodes(self.handle, self.Ne * self.K)
+        _check(code, "dgfs_dg_nodes")
+        return x.reshape(self.Ne, self.K)
+
+    def transport(self, f, rhs=None, stream=None):
+        """f: CUDA tensor [Ne*K, s, N, N, N]; returns the transport part of d_t f."""
+        import torch
+        if rhs is None:
+            rhs = torch.empty_like(f)
+        _check(dgfs_dg_transport(self.handle, f.data_ptr(), rhs.data_ptr(), _stream_handle(stream)),
+               "dgfs_dg_transport")
+        return rhs
+
+    def step(self, f, dt, stream=None):
+        """One SSP-RK2 step of the full equation, in place on f."""
+        _check(dgfs_dg_step(self.handle, f.data_ptr(), float(dt), _stream_handle(stream)),
+               "dgfs_dg_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dgfs_dg_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -21,6 +21,7 @@
 // combinations are fused into the transport kernel.
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -52,11 +53,31 @@ struct DGKParams {
   const double* num;          // outgoing wall fluxes [2][s]
 };
 
+// 16 bytes of consecutive velocities per thread: 4 floats or 2 doubles.  N^2 is a multiple of
+// 4 for the even grids the library supports, so a thread's velocities share their v_x index
+// (and their reflected block); every access is a 16-byte vector access.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vload(const T* p, T (&x)[Vec16<T>::n]) {
+  const typename Vec16<T>::type v = *reinterpret_cast<const typename Vec16<T>::type*>(p);
+  memcpy(x, &v, sizeof(v));
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, const T (&x)[Vec16<T>::n]) {
+  typename Vec16<T>::type v;
+  memcpy(&v, x, sizeof(v));
+  *reinterpret_cast<typename Vec16<T>::type*>(p) = v;
+}
+
 // MODE 0: out = transport rhs; 1: out = F + dt (rhs + C); 2: out = F0/2 + (F + dt (rhs + C))/2
 template <typename T, int MODE, int K>
 __global__ void __launch_bounds__(256) dg_transport_kernel(const DGKParams p) {
+  constexpr int V = Vec16<T>::n;
   const size_t N3 = size_t(p.N) * p.N * p.N;
-  const size_t v = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  const size_t v = (blockIdx.x * size_t(blockDim.x) + threadIdx.x) * V;  // first velocity
   if (v >= N3) return;
   const int e = int(blockIdx.y) / p.s;
   const int i = int(blockIdx.y) % p.s;
@@ -64,42 +85,50 @@ __global__ void __launch_bounds__(256) dg_transport_kernel(const DGKParams p) {
   const int s_ = p.s;
   auto at = [=](int ee, int m) { return ((size_t(ee) * K + m) * s_ + i) * N3 + v; };
   const int a = int(v / (size_t(p.N) * p.N));
-  // the same velocity with v_x -> -v_x (the grid is symmetric: index a -> N - 1 - a)
+  // the same velocities with v_x -> -v_x (the grid is symmetric: index a -> N - 1 - a)
   const size_t v_refl = size_t(static_cast<long long>(v) + static_cast<long long>(p.N - 1 - 2 * a) * p.N * p.N);
   constexpr bool F32 = sizeof(T) == 4;
   const T vx = F32 ? T(p.vx0f + (float(a) + 0.5f) * p.dvf) : T(p.vx0 + (a + 0.5) * p.dv);
 
-  T Fl[K];
+  T Fl[K][V];
 #pragma unroll
-  for (int m = 0; m < K; ++m) Fl[m] = F[at(e, m)];
+  for (int m = 0; m < K; ++m) vload<T>(F + at(e, m), Fl[m]);
 
-  // upwind values at the two faces
-  T up_l = Fl[0], up_r = Fl[K - 1];
+  // upwind values at the two faces (v_x is the same for the thread's velocities)
+  T up_l[V], up_r[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    up_l[j] = Fl[0][j];
+    up_r[j] = Fl[K - 1][j];
+  }
   if (vx > T(0)) {
     if (e > 0) {
-      up_l = F[at(e - 1, K - 1)];
+      vload<T>(F + at(e - 1, K - 1), up_l);
     } else if (p.bc == DGFS_BC_PERIODIC) {
-      up_l = F[at(p.Ne - 1, K - 1)];
+      vload<T>(F + at(p.Ne - 1, K - 1), up_l);
     } else {
-      const double nw = -p.num[i] / p.den[i];
-      const T* W = static_cast<const T*>(p.W);
-      up_l = T(1.0 - p.acc[0]) * F[((size_t(0) * K + 0) * p.s + i) * N3 + v_refl] +
-             T(p.acc[0] * nw) * W[size_t(i) * N3 + v];
+      const T c_w = T(p.acc[0] * (-p.num[i] / p.den[i])), c_s = T(1.0 - p.acc[0]);
+      T fr[V], wv[V];
+      vload<T>(F + (size_t(0) * s_ + i) * N3 + v_refl, fr);
+      vload<T>(static_cast<const T*>(p.W) + size_t(i) * N3 + v, wv);
+#pragma unroll
+      for (int j = 0; j < V; ++j) up_l[j] = c_s * fr[j] + c_w * wv[j];
     }
   }
   if (vx < T(0)) {
     if (e < p.Ne - 1) {
-      up_r = F[at(e + 1, 0)];
+      vload<T>(F + at(e + 1, 0), up_r);
     } else if (p.bc == DGFS_BC_PERIODIC) {
-      up_r = F[at(0, 0)];
+      vload<T>(F + at(0, 0), up_r);
     } else {
-      const double nw = -p.num[p.s + i] / p.den[kMaxS + i];
-      const T* W = static_cast<const T*>(p.W);
-      up_r = T(1.0 - p.acc[1]) * F[((size_t(p.Ne - 1) * K + (K - 1)) * p.s + i) * N3 + v_refl] +
-             T(p.acc[1] * nw) * W[(size_t(p.s) + i) * N3 + v];
+      const T c_w = T(p.acc[1] * (-p.num[s_ + i] / p.den[kMaxS + i])), c_s = T(1.0 - p.acc[1]);
+      T fr[V], wv[V];
+      vload<T>(F + ((size_t(p.Ne) * K - 1) * s_ + i) * N3 + v_refl, fr);
+      vload<T>(static_cast<const T*>(p.W) + (size_t(s_) + i) * N3 + v, wv);
+#pragma unroll
+      for (int j = 0; j < V; ++j) up_r[j] = c_s * fr[j] + c_w * wv[j];
     }
   }
-  const T flux_l = vx * up_l, flux_r = vx * up_r;
 
   T* out = static_cast<T*>(p.out);
   const T* C = static_cast<const T*>(p.C);
@@ -107,21 +136,25 @@ __global__ void __launch_bounds__(256) dg_transport_kernel(const DGKParams p) {
   const T dt = T(p.dt);  // one conversion per thread
 #pragma unroll
   for (int m = 0; m < K; ++m) {
-    T vol = T(0);
-#pragma unroll
-    for (int l = 0; l < K; ++l) vol += (F32 ? T(p.Sf[m * kMaxK + l]) : T(p.S[m * kMaxK + l])) * Fl[l];
-    T r = vx * vol;
-    if (m == K - 1) r -= flux_r;
-    if (m == 0) r += flux_l;
-    r *= F32 ? T(p.coeff[m]) : T(p.coef[m]);
     const size_t o = at(e, m);
-    if constexpr (MODE == 0) {
-      out[o] = r;
-    } else if constexpr (MODE == 1) {
-      out[o] = Fl[m] + dt * (r + C[o]);
-    } else {
-      out[o] = T(0.5) * F0[o] + T(0.5) * (Fl[m] + dt * (r + C[o]));
+    const T cm = F32 ? T(p.coeff[m]) : T(p.coef[m]);
+    T r[V], c[V], f0[V];
+    if constexpr (MODE != 0) vload<T>(C + o, c);
+    if constexpr (MODE == 2) vload<T>(F0 + o, f0);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      T vol = T(0);
+#pragma unroll
+      for (int l = 0; l < K; ++l) vol += (F32 ? T(p.Sf[m * kMaxK + l]) : T(p.S[m * kMaxK + l])) * Fl[l][j];
+      T rr = vx * vol;
+      if (m == K - 1) rr -= vx * up_r[j];
+      if (m == 0) rr += vx * up_l[j];
+      rr *= cm;
+      if constexpr (MODE == 0) r[j] = rr;
+      else if constexpr (MODE == 1) r[j] = Fl[m][j] + dt * (rr + c[j]);
+      else r[j] = T(0.5) * f0[j] + T(0.5) * (Fl[m][j] + dt * (rr + c[j]));
     }
+    vstore<T>(out + o, r);
   }
 }
 
@@ -252,7 +285,8 @@ int launch_transport(dgfs_dg_plan_s& d, int mode, const void* F, const void* F0,
     dg_wall_flux_kernel<T><<<2 * p.s, 256, 0, st>>>(static_cast<const T*>(F), d.Ne, d.K, p.s, p.N, kp.vx0, kp.dv,
                                                    d.d_num);
   }
-  const dim3 grid(unsigned((N3 + 255) / 256), unsigned(d.Ne * p.s));
+  const size_t threads = N3 / (16 / sizeof(T));  // one 16-byte vector of velocities each
+  const dim3 grid(unsigned((threads + 255) / 256), unsigned(d.Ne * p.s));
   switch (d.K) {
     case 2: launch_k<T, 2>(mode, grid, kp, st); break;
     case 3: launch_k<T, 3>(mode, grid, kp, st); break;

@@ -56,16 +56,31 @@ def flops_per_transform(N):
     return 5.0 * n3 * np.log2(n3)
 
 
+# the sources that define the collision kernel's code and launch shape
+COLLISION_KERNEL_SOURCES = ("collision_kernel.cuh", "fft_line.cuh", "collision_f32.cu", "collision_f64.cu",
+                            "dgfs_internal.h", "tuned_shapes.h")
+
+
 def kernel_sources_sha1():
-    """SHA-1 over the CUDA sources, to tie a stored ncu traffic figure to the kernel it measured."""
+    """SHA-1 over the collision kernel's sources, to tie a stored ncu traffic figure to the
+    kernel it measured."""
     import hashlib
     d = os.path.join(ROOT, "paper_1903_03056_gb300", "csrc")
     h = hashlib.sha1()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
+    for name in COLLISION_KERNEL_SOURCES:
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (generated file), else the
+    earlier measurement on a GB300."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def measured_traffic(kernel):
@@ -274,6 +289,40 @@ def serving_leg(args):
     return out
 
 
+def dg_leg(torch, w, stream, Ne=1024, K=4):
+    """The 1D DG path on Ne elements of K GLL nodes (Ne K = 4096 nodes of the batch's grid and
+    species) between Maxwell walls: one transport pass (HBM-bound kernel, algorithmic bytes = the
+    state read once and the right-hand side written once) and one full SSP-RK2 step (two
+    transport passes and two collision evaluations of all nodes), FP32."""
+    from paper_1903_03056_gb300 import dgfs, synth
+    B = Ne * K
+    f = synth.batch_distribution(w, nodes=range(min(B, w.batch)))
+    f = np.concatenate([f] * (B // len(f) + 1))[:B]
+    with torch.cuda.stream(stream):
+        fd = torch.from_numpy(f.astype(np.float32)).cuda()
+        rhs = torch.empty_like(fd)
+    stream.synchronize()
+    coll = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho,
+                     precision="fp32", flags=dgfs.DGFS_SUM_SPECIES, max_batch=B)
+    dgp = dgfs.DGPlan(coll, Ne, K, 0.0, 1.0, bc="walls", Tw=(0.9, 1.2),
+                      uw=((0.0, 0.2, 0.0), (0.0, -0.2, 0.0)), acc=(1.0, 1.0))
+    ms_t = time_steps(torch, lambda: dgp.transport(fd, rhs, stream), 10, 3, stream)
+    ms_s = time_steps(torch, lambda: dgp.step(fd, 1e-3, stream), 1, 0, stream)
+    peak, how = hbm_peak_gbs()
+    nbytes = 2 * fd.numel() * fd.element_size()
+    gbs = nbytes / (ms_t * 1e-3) / 1e9
+    out = {"config": {"elements": Ne, "gll_nodes": K, "nodes": B, "N": w.N, "species": w.s,
+                      "bc": "Maxwell walls (diffuse)", "dtype": "f32"},
+           "transport_ms": ms_t, "step_ms": ms_s,
+           "transport_roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "peak_source": how,
+                                  "bytes_per_launch": nbytes, "kernel": "dg_transport_kernel<float,0,4>"}}
+    dgp.close()
+    coll.close()
+    del fd, rhs
+    return out
+
+
 def gpu_arm(args):
     import torch
     from paper_1903_03056_gb300 import build, dgfs, synth
@@ -353,6 +402,10 @@ def gpu_arm(args):
         plan64.close()
         del fd, Qd
 
+    dg = None
+    if not args.no_dg and world == 1:
+        dg = dg_leg(torch, w, stream)
+
     serving = None
     if not args.no_serving and world == 1:
         del f32
@@ -372,7 +425,7 @@ def gpu_arm(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_dict(w), "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "fp64": fp64, "serving": serving}
+                "clocks": clk.summary(), "fp64": fp64, "dg": dg, "serving": serving}
         print(json.dumps(line), flush=True)
     plan32.close()
     if dist is not None:
@@ -389,6 +442,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--serve-calib", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-sm-share", type=float, default=0.5)

@@ -7,8 +7,9 @@
 //           are inverse-transformed along x (the x phase is shared by the group);
 //   step B  plane pass over (y, z): per entry, the y and z phases are applied, the inverse
 //           transforms along y and z finish a_e and b_e on the plane, and
-//           P += w_e a_e b_e accumulates in registers; after the last group P is transformed
-//           forward along z and y;
+//           P += w_e a_e b_e accumulates in registers (entries with the previous entry's
+//           sigma_y reuse its y pass where a third plane buffer fits); after the last group
+//           P is transformed forward along z and y;
 //   step C  pencil pass along x: forward transform of P, then Q_hat^+_(ij) += w_rho F^(ij) P_hat
 //           (and Q_hat^+_(ji) += w_rho F^(ji) P_hat for a cross pair).
 //
@@ -16,8 +17,10 @@
 // convolution of Sec. 4) and writes it.  The 3D transforms are split into a pencil pass
 // (x, strided by N^2) and a plane pass (y, z, contiguous), each line transformed in the
 // registers of one thread; the planes of a volume are spread over the cluster's CTAs and the
-// pencils likewise, with the volumes in an L2-resident per-cluster workspace and cluster
-// barriers between passes.
+// pencils likewise, with cluster barriers between passes.  The volumes live in a per-cluster
+// workspace accessed through L2 only; when the workspaces of all resident clusters exceed L2
+// (N >= 24) part of them streams through HBM, and each plane is prefetched into L2 one read
+// ahead of its use.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -267,14 +267,16 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
 
 def serving_leg(args):
     """The mixed request stream: N in {16, 24, 32, 48}, s in {2, 3}, masses U[1, 4], VHS
-    omega U[0.5, 1], batches of 1..4096 nodes, FP32, 120 GB HBM budget, 8 slots.  A closed-loop
+    omega U[0.5, 1], batches of 1..4096 nodes, FP32, 120 GB HBM budget, 8 slots, requests
+    served in chunks of ~50 ms of device work, shortest remaining work first.  A closed-loop
     run of the first requests measures the mix's throughput; the Poisson stream then arrives
     at 75% of it."""
     from paper_1903_03056_gb300 import serve
     budget = 120 << 30
     ex = serve.GpuExecutor(slots=8, sm_share=args.serve_sm_share)
     warm_s = ex.warmup()
-    eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8)
+    chunk = args.serve_chunk_s if args.serve_chunk_s > 0 else None
+    eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8, chunk_s=chunk, policy=args.serve_policy)
     calib = serve.mixed_stream(args.serve_calib, math.inf, seed=5000)
     st0 = eng.run(calib)
     rate = 0.75 * st0.n / st0.makespan
@@ -283,7 +285,8 @@ def serving_leg(args):
     out = st.as_dict()
     out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
                 "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
-                "sm_share": args.serve_sm_share, "warmup_s": warm_s,
+                "sm_share": args.serve_sm_share, "warmup_s": warm_s, "policy": args.serve_policy,
+                "chunk_s": chunk,
                 "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
                        "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
     return out
@@ -445,7 +448,10 @@ def main():
     ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--serve-calib", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=64)
-    ap.add_argument("--serve-sm-share", type=float, default=0.5)
+    ap.add_argument("--serve-sm-share", type=float, default=1.0)
+    ap.add_argument("--serve-chunk-s", type=float, default=0.05,
+                    help="device seconds per chunk of a request (0: whole requests)")
+    ap.add_argument("--serve-policy", default="srpt", choices=["srpt", "fifo"])
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -26,7 +26,9 @@
  * Streams   : device entry points are asynchronous and ordered on the given cudaStream_t
  *             (NULL = legacy default stream); they never synchronise the device.
  * Threads   : a plan is not thread-safe; distinct plans may run concurrently on distinct
- *             streams.
+ *             streams.  Evaluations of one plan use its single workspace: one enqueued on a
+ *             different stream than the plan's previous evaluation first waits for that
+ *             evaluation (cudaStreamWaitEvent), so they never overlap on the device.
  * Errors    : 0 on success, a negative DGFS_ERR_* code otherwise; dgfs_strerror() names it.
  *             Arguments are checked before any work is enqueued.
  */

@@ -27,6 +27,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<std::uintptr_t>(p) & 15
 // returns the number of kernels enqueued through *launches
 int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
   p.last_launches = 0;
+  // the plan's workspace and work counter serve one kernel at a time: an evaluation enqueued
+  // on another stream than the previous one waits for it
+  if (p.has_eval && st != p.last_stream && cudaStreamWaitEvent(st, p.last_eval, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
   const bool sum = (p.flags & DGFS_SUM_SPECIES) != 0u;
   if (sum && (batch > p.max_batch || !p.d_Qfull)) return DGFS_ERR_BUDGET;
   void* Qfull = sum ? p.d_Qfull : Q;
@@ -47,6 +53,7 @@ int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
     return DGFS_ERR_CUDA;
   }
   p.has_eval = true;
+  p.last_stream = st;
   return DGFS_OK;
 }
 

@@ -73,6 +73,7 @@ struct Plan {
   int device = 0;
   cudaStream_t home = nullptr;     // the plan's own stream: table builds, stream-ordered alloc/free
   cudaEvent_t last_eval = nullptr; // recorded after every evaluation
+  cudaStream_t last_stream = nullptr;  // the stream of that evaluation
   bool has_eval = false;
   int N = 0;
   double L = 0;

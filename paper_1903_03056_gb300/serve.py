@@ -19,6 +19,13 @@ Loop (one host thread, ``ServingEngine.run``):
 The budget covers admitted requests (plan tables, workspace, input and output); plans built
 ahead for waiting requests are bounded by the prefetch depth.
 
+Chunked mode (``chunk_s`` set): an admitted request does not hold a slot.  A free slot takes
+the next chunk of some admitted request -- consecutive nodes worth about ``chunk_s`` seconds
+of device work by a cost model -- chosen by ``policy``: "srpt" takes the request with the
+least remaining work (small requests overtake large ones between chunks), "fifo" the
+earliest.  Chunks of one request may run on several slots at once; results do not depend on
+how a batch is split, since every node is evaluated independently.
+
 Latency = completion - arrival.  The executor is pluggable: ``GpuExecutor`` drives the CUDA
 library, ``FakeExecutor`` (tests) models durations on the CPU.
 """
@@ -51,6 +58,8 @@ class Request:
     done: float = None
     bytes: int = 0
     slot: int = -1
+    next_node: int = 0      # chunked mode: first node not yet submitted
+    nodes_done: int = 0     # chunked mode: nodes whose chunks completed
 
     @property
     def s(self):
@@ -83,6 +92,17 @@ def mixed_stream(n_requests, rate, seed=5000, sizes=(16, 24, 32, 48), max_batch=
         out.append(Request(k, t if math.isfinite(rate) else 0.0, N, L_FOR_N[N], masses, omega, 12,
                            N // 2, batch, pool_offset=int(rng.integers(0, 1 << 20))))
     return out
+
+
+# seconds per node of one evaluation on the whole device, by the transform count
+# s^2 N_rho M N^3 log2 N^3 (calibrated on the 4096-node N=32, s=2, N_rho=16, M=12 batch:
+# 79 us per node)
+COST_PER_TRANSFORM_POINT = 79e-6 / (4 * 16 * 12 * 32 ** 3 * 15)
+
+
+def cost_per_node(r):
+    n3 = r.N ** 3
+    return COST_PER_TRANSFORM_POINT * r.s * r.s * r.N_rho * r.M * n3 * math.log2(n3)
 
 
 def percentile(values, p):
@@ -121,14 +141,20 @@ class Stats:
 
 
 class ServingEngine:
-    def __init__(self, executor, budget_bytes, slots=8, prefetch=8):
+    def __init__(self, executor, budget_bytes, slots=8, prefetch=8, chunk_s=None, policy="srpt"):
+        if policy not in ("srpt", "fifo"):
+            raise ValueError(policy)
         self.ex = executor
         self.budget = int(budget_bytes)
         self.slots = slots
         self.prefetch = prefetch
+        self.chunk_s = chunk_s
+        self.policy = policy
 
     def run(self, requests, poll_s=50e-6):
         """Serve `requests` (arrival times relative to the start); returns Stats."""
+        if self.chunk_s is not None:
+            return self._run_chunked(requests, poll_s)
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         arrivals = collections.deque(reqs)
         pending = collections.deque()       # arrived, waiting for admission (FIFO)
@@ -194,6 +220,103 @@ class ServingEngine:
                      peak_inflight=peak_inflight, budget=self.budget)
 
 
+def _chunked_engine_run(self, requests, poll_s):
+    """Chunked loop (see the module docstring); returns Stats."""
+    reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+    arrivals = collections.deque(reqs)
+    pending = collections.deque()       # arrived, waiting for admission (FIFO)
+    plans = {}                          # rid -> future of the plan
+    active = []                         # admitted, nodes left to submit or running
+    running = {}                        # slot -> (request, lo, hi)
+    free_slots = list(range(self.slots))
+    in_use = 0
+    peak_bytes, peak_inflight = 0, 0
+    builder = ThreadPoolExecutor(max_workers=2)
+    t0 = time.perf_counter()
+
+    def pick():
+        # one chunk per plan at a time: a plan's evaluations share its workspace and the library
+        # serialises them, so a second chunk of the same plan would only hold a slot
+        busy = {r.plan_key for (r, _, _) in running.values()}
+        cand = [r for r in active if r.next_node < r.batch and r.plan_key not in busy]
+        if not cand:
+            return None
+        if self.policy == "fifo":
+            return min(cand, key=lambda r: (r.arrival, r.rid))
+        return min(cand, key=lambda r: ((r.batch - r.next_node) * cost_per_node(r), r.arrival, r.rid))
+
+    try:
+        while arrivals or pending or active:
+            now = time.perf_counter() - t0
+            while arrivals and arrivals[0].arrival <= now:
+                pending.append(arrivals.popleft())
+            for r in list(pending)[: self.prefetch]:
+                if r.rid not in plans:
+                    plans[r.rid] = builder.submit(self.ex.prepare, r)
+            # admission in arrival order under the memory budget (no slot needed)
+            while pending:
+                r = pending[0]
+                fut = plans.get(r.rid)
+                if fut is None or not fut.done():
+                    break
+                need = fut.result()
+                if need > self.budget:
+                    raise RuntimeError("request %d needs %d bytes, budget %d" % (r.rid, need, self.budget))
+                if in_use + need > self.budget:
+                    break
+                pending.popleft()
+                r.bytes = need
+                r.admitted = time.perf_counter() - t0
+                r.next_node, r.nodes_done = 0, 0
+                in_use += need
+                self.ex.begin(r)
+                active.append(r)
+                peak_bytes = max(peak_bytes, in_use)
+            # fill free slots with chunks
+            while free_slots:
+                r = pick()
+                if r is None:
+                    break
+                n = max(1, int(self.chunk_s / cost_per_node(r)))
+                lo, hi = r.next_node, min(r.batch, r.next_node + n)
+                r.next_node = hi
+                slot = free_slots.pop()
+                self.ex.submit_chunk(r, slot, lo, hi)
+                running[slot] = (r, lo, hi)
+                peak_inflight = max(peak_inflight, len(running))
+            # chunk completions
+            for slot, (r, lo, hi) in list(running.items()):
+                if self.ex.chunk_done(slot):
+                    del running[slot]
+                    free_slots.append(slot)
+                    r.nodes_done += hi - lo
+                    if r.nodes_done == r.batch:
+                        r.done = time.perf_counter() - t0
+                        self.ex.finish(r)
+                        plans.pop(r.rid, None)
+                        in_use -= r.bytes
+                        active.remove(r)
+            if not running and not pending and not active and arrivals:
+                wait = arrivals[0].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+            else:
+                time.sleep(poll_s)
+    finally:
+        builder.shutdown(wait=True)
+    lat = [r.latency for r in reqs]
+    first = min(r.arrival for r in reqs)
+    makespan = max(r.done for r in reqs) - first
+    return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=makespan,
+                 p50=percentile(lat, 50), p99=percentile(lat, 99),
+                 mean_latency=sum(lat) / len(lat), peak_bytes=peak_bytes,
+                 peak_inflight=peak_inflight, budget=self.budget,
+                 extra={"policy": self.policy, "chunk_s": self.chunk_s})
+
+
+ServingEngine._run_chunked = _chunked_engine_run
+
+
 class FakeExecutor:
     """CPU model of the device for scheduler tests: a request occupies its slot for
     `seconds_per_node * batch` and needs a fixed number of bytes per node."""
@@ -223,6 +346,30 @@ class FakeExecutor:
             self.active -= 1
             self.log.append(("release", r.rid, r.slot))
 
+    # chunked mode: a chunk of n nodes occupies its slot for seconds_per_node * n
+    def begin(self, r):
+        self.log.append(("begin", r.rid))
+
+    def submit_chunk(self, r, slot, lo, hi):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+            self.log.append(("chunk", r.rid, slot, lo, hi))
+        if not hasattr(self, "_slot_end"):
+            self._slot_end = {}
+        self._slot_end[slot] = time.perf_counter() + self.spn * (hi - lo)
+
+    def chunk_done(self, slot):
+        if time.perf_counter() >= self._slot_end[slot]:
+            with self.lock:
+                self.active -= 1
+            self._slot_end[slot] = float("inf")
+            return True
+        return False
+
+    def finish(self, r):
+        self.log.append(("finish", r.rid))
+
 
 class GpuExecutor:
     """Drives libdgfs: plans from a cache (shared by requests with equal parameters), one
@@ -248,6 +395,7 @@ class GpuExecutor:
         self.sm_share = sm_share
         self.outputs = {}
         self.state = {}
+        self.slot_events = {}
 
     def _pool(self, N, s):
         """Seeded input nodes per (N, s), on the device (bi-Maxwellians with 5% noise)."""
@@ -305,6 +453,36 @@ class GpuExecutor:
             if self.plan_users[r.plan_key] == 0:
                 self.plans.pop(r.plan_key).close()
                 del self.plan_users[r.plan_key]
+
+    # chunked mode: inputs and outputs of the whole request at admission, one launch per chunk
+    def begin(self, r):
+        torch = self.torch
+        pool = self._pool(r.N, r.s)
+        with torch.cuda.device(self.dev):
+            idx = (torch.arange(r.batch, device=self.dev) + r.pool_offset) % self.pool_nodes
+            f = pool.index_select(0, idx)
+            Q = torch.empty((r.batch, r.s, r.s, r.N, r.N, r.N), dtype=self.dt, device=self.dev)
+            ready = torch.cuda.Event()
+            ready.record(torch.cuda.current_stream(self.dev))
+        self.state[r.rid] = (f, Q, ready)
+
+    def submit_chunk(self, r, slot, lo, hi):
+        torch = self.torch
+        st = self.streams[slot]
+        f, Q, ready = self.state[r.rid]
+        plan = self.plans[r.plan_key]
+        with torch.cuda.stream(st):
+            st.wait_event(ready)
+            plan.eval_ptr(f[lo].data_ptr(), Q[lo].data_ptr(), hi - lo, st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        self.slot_events[slot] = ev
+
+    def chunk_done(self, slot):
+        return self.slot_events[slot].query()
+
+    def finish(self, r):
+        self.release(r)
 
     def warmup(self, grids=(16, 24, 32, 48), species=(2, 3)):
         """One small evaluation per (N, s) through the same calls as `submit`, so the first

@@ -192,3 +192,23 @@ def test_cuda_graph_replay_matches_direct_launch(flags):
         torch.cuda.synchronize()
         assert torch.equal(Q, ref)
     plan.close()
+
+
+def test_one_plan_on_two_streams_never_overlaps():
+    """A plan owns one workspace: evaluations enqueued alternately on two streams without any
+    host synchronisation must still give the serial result (the library orders them)."""
+    import torch
+    N, L, masses = 16, 6.0, (1.0, 2.0)
+    f = _inputs(N, L, masses, 256, seed=77)
+    plan = dgfs.Plan(N, L, list(masses), 0.5, M=12, N_rho=8, precision="fp32")
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    ref = plan.eval(fd)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.empty_like(ref) for _ in range(6)]
+    for k, Q in enumerate(outs):
+        plan.eval_ptr(fd.data_ptr(), Q.data_ptr(), fd.shape[0], streams[k % 2])
+    torch.cuda.synchronize()
+    for Q in outs:
+        assert torch.equal(Q, ref)
+    plan.close()

@@ -54,15 +54,58 @@ def test_request_larger_than_budget_is_an_error():
 
 
 @pytest.mark.gpu
-def test_each_result_equals_its_result_alone():
+@pytest.mark.parametrize("chunk_s", [None, 2e-4])
+def test_each_result_equals_its_result_alone(chunk_s):
+    """Whole-request and chunked (SRPT) service: every request's output in the mix is bitwise
+    equal to its output evaluated alone."""
     import torch
     from paper_1903_03056_gb300 import build
     build.build()
     ex = serve.GpuExecutor(slots=4, keep_outputs=True)
     reqs = _small_stream(16, 400.0, seed=11)
-    st = serve.ServingEngine(ex, budget_bytes=8 << 30, slots=4).run(reqs)
+    st = serve.ServingEngine(ex, budget_bytes=8 << 30, slots=4, chunk_s=chunk_s).run(reqs)
     print("serving mix:", st.as_dict())
     assert st.peak_inflight > 1
     for r in reqs:
         alone = ex.run_alone(r)
         assert torch.equal(ex.outputs[r.rid], alone), r.rid
+
+
+def test_chunked_srpt_lets_small_requests_overtake_a_large_one():
+    """Chunked mode: a large request admitted first is split into chunks, and a small request
+    that arrives later finishes long before it (FIFO whole-request service would finish it
+    after the large one); every node of every request is submitted exactly once."""
+    fake = serve.FakeExecutor(seconds_per_node=2e-5)
+    big = serve.Request(0, 0.0, 16, 6.0, (1.0, 2.0), 0.7, 12, 8, 4000)
+    small = serve.Request(1, 0.01, 16, 6.0, (1.0, 3.0), 0.7, 12, 8, 20)
+    eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=1, chunk_s=0.005, policy="srpt")
+    st = eng.run([big, small])
+    assert small.done < big.done
+    assert small.latency < 0.25 * big.latency
+    covered = {}
+    for ev in fake.log:
+        if ev[0] == "chunk":
+            _, rid, slot, lo, hi = ev
+            covered.setdefault(rid, []).append((lo, hi))
+    for r in (big, small):
+        spans = sorted(covered[r.rid])
+        assert spans[0][0] == 0 and spans[-1][1] == r.batch
+        assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+    assert st.n == 2
+
+
+def test_chunked_fifo_serves_in_arrival_order():
+    fake = serve.FakeExecutor(seconds_per_node=2e-5)
+    big = serve.Request(0, 0.0, 16, 6.0, (1.0, 2.0), 0.7, 12, 8, 2000)
+    small = serve.Request(1, 0.01, 16, 6.0, (1.0, 3.0), 0.7, 12, 8, 20)
+    eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=1, chunk_s=0.005, policy="fifo")
+    eng.run([big, small])
+    assert big.done < small.done
+
+
+def test_chunked_mode_runs_one_chunk_per_plan_at_a_time():
+    fake = serve.FakeExecutor(seconds_per_node=1e-5)
+    reqs = [serve.Request(k, 0.0, 16, 6.0, (1.0, 2.0), 0.7, 12, 8, 300) for k in range(3)]
+    eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=4, chunk_s=0.0005, policy="srpt")
+    eng.run(reqs)
+    assert fake.max_active == 1   # all three share one plan key

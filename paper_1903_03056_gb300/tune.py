@@ -36,7 +36,8 @@ CANDIDATES = {
     16: [(1, 8, 3), (1, 8, 1), (2, 4, 3), (1, 4, 4), (1, 16, 1)],
     24: [(2, 4, 3), (2, 12, 1), (1, 8, 2), (2, 4, 2)],
     32: [(2, 4, 1), (4, 4, 1), (1, 8, 1), (2, 8, 1), (2, 2, 2), (4, 2, 1), (8, 2, 1), (8, 4, 1),
-         (4, 8, 1)],
+         (4, 8, 1), (2, 2, 4), (4, 2, 4), (2, 1, 8), (1, 2, 4), (2, 4, 3), (1, 4, 3), (4, 4, 3),
+         (2, 2, 6)],
     48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2), (4, 4, 1), (4, 2, 1), (8, 2, 1)],
 }
 

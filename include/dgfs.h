@@ -190,16 +190,23 @@ int dgfs_eval_collision_noalloc(const dgfs_plan_desc* desc, const void* f_dev, v
 typedef struct dgfs_dg_plan_s* dgfs_dg_plan; /* opaque, owned by the library */
 
 #define DGFS_BC_PERIODIC 0 /* f(x1) continues at x0 */
-#define DGFS_BC_WALLS 1    /* Maxwell walls at x0 (outward normal -x) and x1 (+x) */
+#define DGFS_BC_WALLS 1    /* boundary sides at x0 (outward normal -x) and x1 (+x), each a
+                              Maxwell wall or an in-flow boundary (side[]) */
+#define DGFS_SIDE_WALL 0   /* Maxwell wall condition (Sec. 2) */
+#define DGFS_SIDE_INFLOW 1 /* in-flow equilibrium condition (Sec. 2): entering particles of
+                              species i follow n_in_i (m_i / (pi T))^(3/2) exp(-m_i |v - u|^2 / T) */
 
 typedef struct {
   int Ne;          /* elements, >= 1 */
   int K;           /* GLL nodes per element, 2..8 */
   double x0, x1;   /* physical domain, x0 < x1 */
   int bc;          /* DGFS_BC_PERIODIC or DGFS_BC_WALLS */
-  double Tw[2];    /* wall temperatures (left, right), > 0; DGFS_BC_WALLS only */
-  double uw[6];    /* wall velocities (left x, y, z, right x, y, z); the x components are 0 */
-  double acc[2];   /* accommodation coefficients in [0, 1]: 1 diffuse, 0 specular */
+  double Tw[2];    /* side temperatures (left, right), > 0; DGFS_BC_WALLS only */
+  double uw[6];    /* side velocities (left x, y, z, right x, y, z); 0 x components for walls */
+  double acc[2];   /* wall accommodation coefficients in [0, 1]: 1 diffuse, 0 specular */
+  int side[2];     /* DGFS_SIDE_WALL or DGFS_SIDE_INFLOW per side */
+  const double* n_in; /* nullable [2 * s] in-flow densities (left side's s, then right's);
+                         required for an in-flow side, >= 0 */
 } dgfs_dg_desc;
 
 /* Build a DG plan on top of a collision plan, which supplies the velocity grid (N, L),

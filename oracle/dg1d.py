@@ -81,12 +81,17 @@ def collision_tensor(K, h):
 class DG1D:
     """Ne uniform elements on [x0, x1], K GLL nodes each, velocity grid of ``prob``.
 
-    bc = "periodic", or "walls": Maxwell walls at x0 (outward normal -x) and x1 (+x), with
-    temperature Tw[side], velocity uw[side] (3-vector; its x component must be 0) and
-    accommodation acc[side] (1 = diffuse, 0 = specular)."""
+    bc = "periodic", or "walls": boundary sides at x0 (outward normal -x) and x1 (+x).  Side k
+    is a Maxwell wall (side_kind[k] = "wall") with temperature Tw[k], velocity uw[k] (3-vector;
+    its x component must be 0) and accommodation acc[k] (1 = diffuse, 0 = specular), or an
+    in-flow equilibrium boundary (side_kind[k] = "inflow", Sec. 2) whose entering particles
+    follow the Maxwellian of densities n_in[k][i], temperature Tw[k] and velocity uw[k]."""
 
     def __init__(self, prob, Ne, K, x0=0.0, x1=1.0, bc="periodic", Tw=(1.0, 1.0),
-                 uw=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), acc=(1.0, 1.0)):
+                 uw=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), acc=(1.0, 1.0),
+                 side_kind=("wall", "wall"), n_in=None):
+        self.side_kind = tuple(side_kind)
+        self.n_in = None if n_in is None else np.asarray(n_in, dtype=np.float64)
         self.prob, self.Ne, self.K = prob, Ne, K
         self.x0, self.x1 = float(x0), float(x1)
         self.h = (self.x1 - self.x0) / Ne
@@ -118,6 +123,15 @@ class DG1D:
         n_out = -1.0 if side == 0 else 1.0
         out = np.array(f_int, copy=True)
         Tw, uw, a = self.Tw[side], self.uw[side], self.acc[side]
+        if self.side_kind[side] == "inflow":
+            # in-flow equilibrium (Sec. 2): n_in (m / (pi T))^(3/2) exp(-m |v - u|^2 / T) for
+            # entering velocities v . n < 0
+            incoming = self.vx * n_out < 0
+            for i, m in enumerate(self.prob.masses):
+                d2 = sum((self.V[d] - uw[d]) ** 2 for d in range(3))
+                inflow = self.n_in[side][i] * (m / (np.pi * Tw)) ** 1.5 * np.exp(-m * d2 / Tw)
+                out[i] = np.where(incoming, inflow, f_int[i])
+            return out
         cn = self.vx * n_out                                        # (v - u_w) . n, u_w . n = 0
         incoming = cn < 0
         for i, m in enumerate(self.prob.masses):

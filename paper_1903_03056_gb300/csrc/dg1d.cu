@@ -40,6 +40,8 @@ struct DGKParams {
   double den[2 * kMaxS];      // wall flux denominators [side][species]
   double vx0, dv;             // v_x of velocity index a: vx0 + (a + 1/2) dv
   double dt;
+  int inflow[2];              // side is an in-flow boundary
+  double cin[2 * kMaxS];      // in-flow coefficient n_in (m / (pi T))^(3/2) [side][species]
   // the same coefficients rounded once to FP32 for the FP32 kernel (GB300's FP64 rate is a
   // small fraction of its FP32 rate, so the FP32 kernel does no FP64 arithmetic per element)
   float Sf[kMaxK * kMaxK];
@@ -107,7 +109,8 @@ __global__ void __launch_bounds__(256) dg_transport_kernel(const DGKParams p) {
     } else if (p.bc == DGFS_BC_PERIODIC) {
       vload<T>(F + at(p.Ne - 1, K - 1), up_l);
     } else {
-      const T c_w = T(p.acc[0] * (-p.num[i] / p.den[i])), c_s = T(1.0 - p.acc[0]);
+      const T c_w = T(p.inflow[0] ? p.cin[i] : p.acc[0] * (-p.num[i] / p.den[i]));
+      const T c_s = T(p.inflow[0] ? 0.0 : 1.0 - p.acc[0]);
       T fr[V], wv[V];
       vload<T>(F + (size_t(0) * s_ + i) * N3 + v_refl, fr);
       vload<T>(static_cast<const T*>(p.W) + size_t(i) * N3 + v, wv);
@@ -121,7 +124,8 @@ __global__ void __launch_bounds__(256) dg_transport_kernel(const DGKParams p) {
     } else if (p.bc == DGFS_BC_PERIODIC) {
       vload<T>(F + at(0, 0), up_r);
     } else {
-      const T c_w = T(p.acc[1] * (-p.num[s_ + i] / p.den[kMaxS + i])), c_s = T(1.0 - p.acc[1]);
+      const T c_w = T(p.inflow[1] ? p.cin[kMaxS + i] : p.acc[1] * (-p.num[s_ + i] / p.den[kMaxS + i]));
+      const T c_s = T(p.inflow[1] ? 0.0 : 1.0 - p.acc[1]);
       T fr[V], wv[V];
       vload<T>(F + ((size_t(p.Ne) * K - 1) * s_ + i) * N3 + v_refl, fr);
       vload<T>(static_cast<const T*>(p.W) + (size_t(s_) + i) * N3 + v, wv);
@@ -343,10 +347,20 @@ int dgfs_dg_create(const dgfs_dg_desc* desc, dgfs_plan collision, dgfs_dg_plan* 
   if (desc->bc != DGFS_BC_PERIODIC && desc->bc != DGFS_BC_WALLS) return DGFS_ERR_INVALID_ARG;
   if (desc->bc == DGFS_BC_WALLS) {
     for (int side = 0; side < 2; ++side) {
-      if (!(desc->Tw[side] > 0.0) || !std::isfinite(desc->Tw[side]) || !(desc->acc[side] >= 0.0) ||
-          !(desc->acc[side] <= 1.0) || desc->uw[3 * side] != 0.0 || !std::isfinite(desc->uw[3 * side + 1]) ||
-          !std::isfinite(desc->uw[3 * side + 2]))
+      const int kind = desc->side[side];
+      if (kind != DGFS_SIDE_WALL && kind != DGFS_SIDE_INFLOW) return DGFS_ERR_INVALID_ARG;
+      if (!(desc->Tw[side] > 0.0) || !std::isfinite(desc->Tw[side]) || !std::isfinite(desc->uw[3 * side]) ||
+          !std::isfinite(desc->uw[3 * side + 1]) || !std::isfinite(desc->uw[3 * side + 2]))
         return DGFS_ERR_INVALID_ARG;
+      if (kind == DGFS_SIDE_WALL &&
+          (!(desc->acc[side] >= 0.0) || !(desc->acc[side] <= 1.0) || desc->uw[3 * side] != 0.0))
+        return DGFS_ERR_INVALID_ARG;
+      if (kind == DGFS_SIDE_INFLOW) {
+        if (!desc->n_in) return DGFS_ERR_INVALID_ARG;
+        for (int i = 0; i < p.s; ++i)
+          if (!(desc->n_in[side * p.s + i] >= 0.0) || !std::isfinite(desc->n_in[side * p.s + i]))
+            return DGFS_ERR_INVALID_ARG;
+      }
     }
   }
   if (long(Ne) * K > 1 << 30) return DGFS_ERR_INVALID_ARG;
@@ -385,26 +399,31 @@ int dgfs_dg_create(const dgfs_dg_desc* desc, dgfs_plan collision, dgfs_dg_plan* 
   const size_t N3 = size_t(N) * N * N;
   DevGuard g(p.device);
   if (!g.ok) { release(d); return DGFS_ERR_CUDA; }
-  // wall Maxwellian shapes exp(-m_i |v - u_w|^2 / T_w) and the denominators of n_w in FP64
+  // side Maxwellian shapes exp(-m_i |v - u|^2 / T); for walls also the denominators of n_w
+  // in FP64, for in-flow sides the constant factor n_in (m_i / (pi T))^(3/2)
   std::vector<double> Wd(2 * size_t(p.s) * N3, 0.0);
   if (desc->bc == DGFS_BC_WALLS) {
     for (int side = 0; side < 2; ++side) {
-      kp.acc[side] = desc->acc[side];
+      const bool inflow = desc->side[side] == DGFS_SIDE_INFLOW;
+      kp.inflow[side] = inflow ? 1 : 0;
+      kp.acc[side] = inflow ? 0.0 : desc->acc[side];
       const double n_out = side == 0 ? -1.0 : 1.0;
+      const double* u = &desc->uw[3 * side];
       for (int i = 0; i < p.s; ++i) {
         double den = 0.0;
         for (size_t v = 0; v < N3; ++v) {
           const int a = int(v / (size_t(N) * N)), b = int((v / N) % N), c = int(v % N);
           const double vx = kp.vx0 + (a + 0.5) * kp.dv, vy = kp.vx0 + (b + 0.5) * kp.dv,
                        vz = kp.vx0 + (c + 0.5) * kp.dv;
-          const double d2 = vx * vx + (vy - desc->uw[3 * side + 1]) * (vy - desc->uw[3 * side + 1]) +
-                            (vz - desc->uw[3 * side + 2]) * (vz - desc->uw[3 * side + 2]);
+          const double d2 = (vx - u[0]) * (vx - u[0]) + (vy - u[1]) * (vy - u[1]) + (vz - u[2]) * (vz - u[2]);
           const double wv = std::exp(-p.mass[i] * d2 / desc->Tw[side]);
           Wd[(size_t(side) * p.s + i) * N3 + v] = wv;
           const double cn = vx * n_out;
           if (cn < 0.0) den += cn * wv;
         }
-        kp.den[side * kMaxS + i] = den;
+        kp.den[side * kMaxS + i] = inflow ? 1.0 : den;
+        kp.cin[side * kMaxS + i] =
+            inflow ? desc->n_in[side * p.s + i] * std::pow(p.mass[i] / (M_PI * desc->Tw[side]), 1.5) : 0.0;
       }
     }
   }

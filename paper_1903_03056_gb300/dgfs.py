@@ -31,6 +31,8 @@ DGFS_SUM_SPECIES = 2
 DGFS_LOSS_ACCURATE = 4
 DGFS_BC_PERIODIC = 0
 DGFS_BC_WALLS = 1
+DGFS_SIDE_WALL = 0
+DGFS_SIDE_INFLOW = 1
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
@@ -58,7 +60,8 @@ class DgfsError(RuntimeError):
 class dgfs_dg_desc(ctypes.Structure):
     _fields_ = [("Ne", ctypes.c_int), ("K", ctypes.c_int), ("x0", ctypes.c_double),
                 ("x1", ctypes.c_double), ("bc", ctypes.c_int), ("Tw", ctypes.c_double * 2),
-                ("uw", ctypes.c_double * 6), ("acc", ctypes.c_double * 2)]
+                ("uw", ctypes.c_double * 6), ("acc", ctypes.c_double * 2),
+                ("side", ctypes.c_int * 2), ("n_in", _dptr)]
 
 
 _lib = None
@@ -330,8 +333,15 @@ class DGPlan:
     """Owns one 1D DG plan built on a collision ``Plan`` (which must outlive it)."""
 
     def __init__(self, collision, Ne, K, x0=0.0, x1=1.0, bc="periodic", Tw=(1.0, 1.0),
-                 uw=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), acc=(1.0, 1.0)):
+                 uw=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)), acc=(1.0, 1.0), side_kind=("wall", "wall"),
+                 n_in=None):
         d = dgfs_dg_desc()
+        for k, kind in enumerate(side_kind):
+            d.side[k] = DGFS_SIDE_INFLOW if kind == "inflow" else DGFS_SIDE_WALL
+        keep = None
+        if n_in is not None:
+            keep = np.ascontiguousarray(np.asarray(n_in, dtype=np.float64).reshape(-1))
+            d.n_in = keep.ctypes.data_as(_dptr)
         d.Ne, d.K, d.x0, d.x1 = int(Ne), int(K), float(x0), float(x1)
         d.bc = DGFS_BC_WALLS if bc == "walls" else DGFS_BC_PERIODIC
         d.Tw[0], d.Tw[1] = float(Tw[0]), float(Tw[1])
@@ -339,6 +349,7 @@ class DGPlan:
             d.uw[k] = float(u)
         d.acc[0], d.acc[1] = float(acc[0]), float(acc[1])
         code, h = dgfs_dg_create(d, collision.handle)
+        del keep
         _check(code, "dgfs_dg_create")
         self.handle, self.collision = h, collision
         self.Ne, self.K = int(Ne), int(K)

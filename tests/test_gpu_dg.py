@@ -23,12 +23,15 @@ def _state(Ne, K, s, N, seed):
     return 0.2 + rng.random((Ne, K, s, N, N, N))
 
 
-def _setup(precision, N, L, masses, Ne, K, bc, Tw, uw, acc, kappa=None, flags=0, M=6, N_rho=4):
+def _setup(precision, N, L, masses, Ne, K, bc, Tw, uw, acc, kappa=None, flags=0, M=6, N_rho=4,
+           side_kind=("wall", "wall"), n_in=None):
     coll = dgfs.Plan(N, L, list(masses), 0.7, M=M, N_rho=N_rho, precision=precision, flags=flags,
                      max_batch=Ne * K, kappa=kappa)
-    dg = dgfs.DGPlan(coll, Ne, K, 0.0, 1.3, bc=bc, Tw=Tw, uw=uw, acc=acc)
+    dg = dgfs.DGPlan(coll, Ne, K, 0.0, 1.3, bc=bc, Tw=Tw, uw=uw, acc=acc, side_kind=side_kind,
+                     n_in=n_in)
     prob = fs.make_problem(N, L, list(masses), omega=0.7, M=M, N_rho=N_rho)
-    ora = dg1d.DG1D(prob, Ne, K, 0.0, 1.3, bc=bc, Tw=Tw, uw=uw, acc=acc)
+    ora = dg1d.DG1D(prob, Ne, K, 0.0, 1.3, bc=bc, Tw=Tw, uw=uw, acc=acc, side_kind=side_kind,
+                    n_in=n_in)
     return coll, dg, ora
 
 
@@ -48,6 +51,27 @@ def test_transport_matches_oracle(precision, bc, acc, K):
     r = dg.transport(fd)
     torch.cuda.synchronize()
     got = r.double().cpu().numpy().reshape(F.shape)
+    ref = ora.transport_rhs(F)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err < (1e-12 if precision == "fp64" else TOL_FP32), err
+    dg.close()
+    coll.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("sides", [("inflow", "wall"), ("inflow", "inflow")])
+def test_transport_with_inflow_sides_matches_oracle(precision, sides):
+    """In-flow equilibrium sides (Sec. 2): drifting in-flow Maxwellians with their own
+    densities, temperature and velocity (x components allowed there)."""
+    import torch
+    N, L, masses, Ne, K = 8, 4.0, (1.0, 2.0), 3, 3
+    uw = ((0.4, 0.1, 0.0), (0.0 if sides[1] == "wall" else -0.3, -0.2, 0.1))
+    coll, dg, ora = _setup(precision, N, L, masses, Ne, K, "walls", Tw=(1.1, 0.9), uw=uw,
+                           acc=(1.0, 0.7), side_kind=sides, n_in=((0.9, 0.4), (0.6, 0.7)))
+    F = _state(Ne, K, 2, N, seed=31)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    fd = torch.from_numpy(F.reshape(Ne * K, 2, N, N, N)).to("cuda", dt)
+    got = dg.transport(fd).double().cpu().numpy().reshape(F.shape)
     ref = ora.transport_rhs(F)
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     assert err < (1e-12 if precision == "fp64" else TOL_FP32), err
@@ -120,7 +144,9 @@ def test_argument_checks():
     coll = dgfs.Plan(8, 4.0, [1.0, 2.0], 0.7, M=6, N_rho=2, precision="fp64")
     bad = [dict(Ne=0, K=3), dict(Ne=2, K=9), dict(Ne=2, K=1),
            dict(Ne=2, K=3, bc="walls", uw=((0.1, 0.0, 0.0), (0.0, 0.0, 0.0))),
-           dict(Ne=2, K=3, bc="walls", acc=(1.2, 1.0)), dict(Ne=2, K=3, bc="walls", Tw=(0.0, 1.0))]
+           dict(Ne=2, K=3, bc="walls", acc=(1.2, 1.0)), dict(Ne=2, K=3, bc="walls", Tw=(0.0, 1.0)),
+           dict(Ne=2, K=3, bc="walls", side_kind=("inflow", "wall")),               # no n_in
+           dict(Ne=2, K=3, bc="walls", side_kind=("inflow", "wall"), n_in=((-1.0, 1.0), (1.0, 1.0)))]
     for kw in bad:
         Ne, K = kw.pop("Ne"), kw.pop("K")
         with pytest.raises(dgfs.DgfsError) as ei:

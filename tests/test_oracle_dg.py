@@ -156,3 +156,21 @@ def test_upwind_flux_takes_the_upstream_trace():
     ref = np.where(dg.vx > 0, (2.0 / dg.h) * dg.vx, 0.0)
     for i in range(2):
         assert np.max(np.abs(r[1, 0, i] - ref)) < 1e-13
+
+
+def test_inflow_boundary_keeps_its_own_maxwellian():
+    """In-flow equilibrium sides (Sec. 2): a uniform state equal to the in-flow Maxwellian
+    (drifting along x, so particles enter through both sides) is steady under transport; a
+    different interior state is not."""
+    prob = _problem()
+    u, T, n = (0.3, 0.1, 0.0), 1.2, (0.8, 0.5)
+    dg = dg1d.DG1D(prob, 3, 3, 0.0, 1.0, bc="walls", Tw=(T, T), uw=(u, u),
+                   side_kind=("inflow", "inflow"), n_in=(n, n))
+    v = fs.velocity_grid(prob.N, prob.L)
+    F = np.zeros((3, 3, 2) + (prob.N,) * 3)
+    for i, m in enumerate(prob.masses):
+        e = [np.exp(-m * (v - u[d]) ** 2 / T) for d in range(3)]
+        M = n[i] * (m / (np.pi * T)) ** 1.5 * e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :]
+        F[:, :, i] = M
+    assert np.max(np.abs(dg.transport_rhs(F))) < 1e-12 * np.max(F)
+    assert np.max(np.abs(dg.transport_rhs(0.5 * F))) > 1e-3 * np.max(F)

@@ -28,7 +28,10 @@
  * Threads   : a plan is not thread-safe; distinct plans may run concurrently on distinct
  *             streams.  Evaluations of one plan use its single workspace: one enqueued on a
  *             different stream than the plan's previous evaluation first waits for that
- *             evaluation (cudaStreamWaitEvent), so they never overlap on the device.
+ *             evaluation (cudaStreamWaitEvent), so they never overlap on the device.  An
+ *             evaluation recorded into a CUDA graph (stream capture) is ordered by the graph
+ *             instead: the caller keeps replays of that graph from overlapping other
+ *             evaluations of the plan, and keeps the plan alive while the graph is used.
  * Errors    : 0 on success, a negative DGFS_ERR_* code otherwise; dgfs_strerror() names it.
  *             Arguments are checked before any work is enqueued.
  */

@@ -28,8 +28,15 @@ bool aligned16(const void* p) { return (reinterpret_cast<std::uintptr_t>(p) & 15
 int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
   p.last_launches = 0;
   // the plan's workspace and work counter serve one kernel at a time: an evaluation enqueued
-  // on another stream than the previous one waits for it
-  if (p.has_eval && st != p.last_stream && cudaStreamWaitEvent(st, p.last_eval, 0) != cudaSuccess) {
+  // on another stream than the previous one waits for it.  Launches recorded into a CUDA graph
+  // (stream capture) are ordered by the graph and leave this bookkeeping alone.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (!capturing && p.has_eval && st != p.last_stream && cudaStreamWaitEvent(st, p.last_eval, 0) != cudaSuccess) {
     cudaGetLastError();
     return DGFS_ERR_CUDA;
   }
@@ -48,6 +55,7 @@ int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
     if ((rc = dgfs::launch_species_sum(p, Qfull, Q, batch, st)) != DGFS_OK) return rc;
     p.last_launches += 1;
   }
+  if (capturing) return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
   if (cudaEventRecord(p.last_eval, st) != cudaSuccess || cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return DGFS_ERR_CUDA;

@@ -465,22 +465,35 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             for (int o = 0; o < 2; ++o) {
               const int pair = o == 0 ? tk.out0 : tk.out1;
               if (pair < 0) break;
-              const double2* F0 = p.Fv + ((size_t(pair) * p.n_rho + q) * p.M + (o == 0 ? m0 : m1)) * N3;
-              const double2* F1 = (o == 0 && tk.out1 < 0 && m1 >= 0)
-                                      ? p.Fv + ((size_t(pair) * p.n_rho + q) * p.M + m1) * N3
-                                      : nullptr;
+              const size_t fo = ((size_t(pair) * p.n_rho + q) * p.M + (o == 0 ? m0 : m1)) * N3;
               CT* acc = o == 0 ? QA : QB;
+              if constexpr (sizeof(T) == 4) {
+                // FP32 table; a halved self pair's slot already holds F(sigma) + F(-sigma)
+                const float2* F0 = static_cast<const float2*>(p.Fv) + fo;
 #pragma unroll
-              for (int n = 0; n < N; ++n) {
-                double2 fw = __ldg(F0 + n * N2 + pp);
-                if (F1) {
-                  const double2 f1 = __ldg(F1 + n * N2 + pp);
-                  fw.x += f1.x;
-                  fw.y += f1.y;
+                for (int n = 0; n < N; ++n) {
+                  CT val = cmul<T>(v[n], __ldg(F0 + n * N2 + pp));
+                  if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
+                  st2<T>(acc + n * N2 + pp, val);
                 }
-                CT val = cmul<T>(v[n], mk<T>(T(fw.x), T(fw.y)));
-                if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
-                st2<T>(acc + n * N2 + pp, val);
+              } else {
+                const double2* Fv = static_cast<const double2*>(p.Fv);
+                const double2* F0 = Fv + fo;
+                const double2* F1 = (o == 0 && tk.out1 < 0 && m1 >= 0)
+                                        ? Fv + ((size_t(pair) * p.n_rho + q) * p.M + m1) * N3
+                                        : nullptr;
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                  double2 fw = __ldg(F0 + n * N2 + pp);
+                  if (F1) {
+                    const double2 f1 = __ldg(F1 + n * N2 + pp);
+                    fw.x += f1.x;
+                    fw.y += f1.y;
+                  }
+                  CT val = cmul<T>(v[n], mk<T>(T(fw.x), T(fw.y)));
+                  if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
+                  st2<T>(acc + n * N2 + pp, val);
+                }
               }
             }
           }
@@ -498,11 +511,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         for (int o = 0; o < 2; ++o) {
           const int pair = o == 0 ? tk.out0 : tk.out1;
           if (pair < 0) break;
-          const double* Fw = p.Fw + (size_t(pair) * p.n_rho + q) * N3;
+          // the table is in the plan's real type (FP32 plans: rounded once at plan creation)
+          const T* Fw = static_cast<const T*>(p.Fw) + (size_t(pair) * p.n_rho + q) * N3;
           CT* acc = o == 0 ? QA : QB;
 #pragma unroll
           for (int n = 0; n < N; ++n) {
-            const T fw = T(__ldg(Fw + n * N2 + pp));
+            const T fw = __ldg(Fw + n * N2 + pp);
             CT val = scale<T>(v[n], fw);
             if (q > 0) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
             st2<T>(acc + n * N2 + pp, val);
@@ -627,14 +641,14 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.groups = pl.d_groups;
   kp.ent_w = pl.d_ent_w;
   kp.phase = pl.d_phase;
-  kp.Fw = pl.d_Fw;
+  kp.Fw = pl.d_Fwf ? static_cast<const void*>(pl.d_Fwf) : static_cast<const void*>(pl.d_Fw);
   kp.Gm = pl.d_Gm;
   kp.scratch = pl.d_scratch;
   kp.phase_smem = pl.shape.phase_smem;
   kp.work_counter = pl.d_counter;
   kp.vss = pl.vss ? 1 : 0;
   kp.M = pl.M;
-  kp.Fv = pl.d_Fv;
+  kp.Fv = pl.d_Fvf ? static_cast<const void*>(pl.d_Fvf) : static_cast<const void*>(pl.d_Fv);
   kp.ent_m = pl.d_ent_m;
   kp.ent_ysh = pl.d_ent_ysh;
   const int items = batch * kp.n_tasks;

@@ -35,7 +35,8 @@ struct KernelParams {
   const GroupDesc* groups;
   const double* ent_w;    // [entries] sigma weight (x2 for halved self pairs)
   const void* phase;      // complex: [task][rho][max_ent][role 2][axis 3][N]
-  const double* Fw;       // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3
+  const void* Fw;         // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3, in the plan's real
+                          // type (FP32 plans: each FP64 value rounded once)
   const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
   void* scratch;          // complex: [clusters][SLOT][N^3]
   int phase_smem;         // 1: the task's phase block of the current rho is staged in smem;
@@ -44,7 +45,9 @@ struct KernelParams {
   // VSS (alpha != 1): sigma-dependent complex gain weights, one forward transform per entry
   int vss;
   int M;
-  const double2* Fv;      // [s*s][n_rho][M][N^3]: w_rho F^(ij)(k, rho, sigma_m) / N^3
+  const void* Fv;         // [s*s][n_rho][M][N^3]: w_rho F^(ij)(k, rho, sigma_m) / N^3, complex
+                          // in the plan's real type; in FP32 plans the slot of a halved self
+                          // pair's representative holds F(sigma) + F(-sigma) (summed in FP64)
   const int* ent_m;       // [entries][2]: design index of the entry and of its antipode (-1)
   const int* ent_ysh;     // [entries]: 1 when the entry has the previous entry's sigma_x and
                           // sigma_y (same group), so both its shifted volumes share that
@@ -105,6 +108,8 @@ struct Plan {
   void* d_Qfull = nullptr;         // full operators staged for DGFS_SUM_SPECIES
   double* d_Fw = nullptr;
   double2* d_Fv = nullptr;         // VSS gain weights (complex)
+  float* d_Fwf = nullptr;          // FP32 plans: the gain tables the kernel reads
+  float2* d_Fvf = nullptr;
   int* d_ent_m = nullptr;
   int* d_ent_ysh = nullptr;
   double* d_Gm = nullptr;
@@ -146,6 +151,9 @@ int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st
 // on-device FP64 weight tables on the plan's stream (tables.cu)
 int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale, int n_loss);
 int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, int n_loss);
+// FP32 copies of the gain tables (d_Fwf from d_Fw, or d_Fvf from d_Fv with the halved self
+// pairs' F(sigma) + F(-sigma) pre-added: pair_sum[m] = antipode to add for representative m)
+int launch_gain_tables_f32(Plan& p, const int* d_pair_sum);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps, const int* d_anti);
 

@@ -568,6 +568,38 @@ int upload_plan(Plan& p) {
     if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale), NL))) return rc;
     if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
   }
+  if (p.precision == DGFS_FP32) {
+    // the FP32 kernel reads FP32 gain tables: each FP64 value rounded once here instead of
+    // converted per element in the kernel (GB300's FP64 rate is a small fraction of its FP32
+    // rate); a halved self pair's representative slot takes F(sigma) + F(-sigma), the sum the
+    // FP64 kernel forms, so the FP32 results are unchanged bit for bit
+    const size_t nF = size_t(P) * NR * (p.vss ? size_t(p.M) : 1) * N3;
+    void* d_pair_sum = nullptr;
+    if (p.vss) {
+      std::vector<int> pair_sum(p.M, -1);
+      for (const TaskDesc& tk : p.tasks)
+        if (tk.i == tk.j && tk.out1 < 0)
+          for (int e = 0; e < tk.n_ent; ++e) {
+            const int m0 = p.ent_m[2 * (tk.ent_off + e)], m1 = p.ent_m[2 * (tk.ent_off + e) + 1];
+            if (m1 >= 0) pair_sum[m0] = m1;
+          }
+      if ((rc = upload(p, pair_sum.data(), pair_sum.size(), &d_pair_sum, tmp))) return rc;
+      tmps.push_back(d_pair_sum);
+      if ((rc = dalloc(p, (void**)&p.d_Fvf, nF * sizeof(float2)))) return rc;
+    } else {
+      if ((rc = dalloc(p, (void**)&p.d_Fwf, nF * sizeof(float)))) return rc;
+    }
+    if ((rc = launch_gain_tables_f32(p, static_cast<const int*>(d_pair_sum)))) return rc;
+    if (p.vss) {
+      cudaFreeAsync(p.d_Fv, p.home);
+      p.d_Fv = nullptr;
+      total = total - nF * sizeof(double2) + nF * sizeof(float2);
+    } else {
+      cudaFreeAsync(p.d_Fw, p.home);
+      p.d_Fw = nullptr;
+      total = total - nF * sizeof(double) + nF * sizeof(float);
+    }
+  }
   for (void* t : tmps) cudaFreeAsync(t, p.home);
   if ((rc = upload(p, p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
   if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
@@ -594,7 +626,7 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter, p.d_rk,      p.d_ent_ysh};
+                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -624,6 +656,8 @@ void free_plan(Plan& p) {
   p.d_kappa = nullptr;
   p.d_Qfull = nullptr;
   p.d_Fv = nullptr;
+  p.d_Fwf = nullptr;
+  p.d_Fvf = nullptr;
   p.d_ent_m = nullptr;
   p.d_ent_ysh = nullptr;
   p.d_counter = nullptr;

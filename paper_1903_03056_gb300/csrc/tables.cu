@@ -77,7 +77,45 @@ __global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int M,
   }
 }
 
+__global__ void gain_to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    dst[i] = float(src[i]);
+}
+
+__global__ void vss_to_f32_kernel(const double2* __restrict__ src, float2* __restrict__ dst, int s, int NR, int M,
+                                  size_t N3, const int* __restrict__ pair_sum) {
+  const size_t n = size_t(s) * s * NR * M * N3;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const size_t k = i % N3;
+    const int m = int((i / N3) % M);
+    const size_t oq = i / (N3 * M);
+    const int o = int(oq / NR);
+    double2 v = src[i];
+    const int am = pair_sum ? pair_sum[m] : -1;
+    if (o / s == o % s && am >= 0) {
+      const double2 w = src[(oq * M + am) * N3 + k];
+      v.x += w.x;
+      v.y += w.y;
+    }
+    dst[i] = make_float2(float(v.x), float(v.y));
+  }
+}
+
 }  // namespace
+
+int launch_gain_tables_f32(Plan& p, const int* d_pair_sum) {
+  const size_t N3 = size_t(p.N) * p.N * p.N;
+  const size_t P = size_t(p.s) * p.s;
+  if (!p.vss) {
+    const size_t n = P * p.N_rho * N3;
+    gain_to_f32_kernel<<<unsigned(n / 256 + 1 < 8192 ? n / 256 + 1 : 8192), 256, 0, p.home>>>(p.d_Fw, p.d_Fwf, n);
+  } else {
+    const size_t n = P * p.N_rho * p.M * N3;
+    vss_to_f32_kernel<<<unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536), 256, 0, p.home>>>(
+        p.d_Fv, p.d_Fvf, p.s, p.N_rho, p.M, N3, d_pair_sum);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
+}
 
 int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, int n_loss) {
   const size_t N3 = size_t(p.N) * p.N * p.N;

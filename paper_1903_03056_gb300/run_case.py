@@ -19,6 +19,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--checksum", action="store_true", help="add the SHA-1 of the output bytes")
+    ap.add_argument("--n-rho", type=int, default=None,
+                    help="override the workload's radial nodes (smaller tables for profiling)")
     a = ap.parse_args()
 
     import torch
@@ -27,6 +29,9 @@ def main():
 
     build.build()
     w = synth.WORKLOADS[a.workload]
+    if a.n_rho is not None:
+        import dataclasses
+        w = dataclasses.replace(w, N_rho=a.n_rho)
     B = a.batch or w.batch
     f = synth.batch_distribution(w, nodes=range(B))
     dt = torch.float32 if a.precision == "fp32" else torch.float64

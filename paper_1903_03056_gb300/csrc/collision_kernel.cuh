@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
       const int jo = o == 0 ? tk.j : tk.i;
       const CT* acc = o == 0 ? QA : QB;
       const CT* Fj = jo == tk.i ? FI : FJs;
-      const double* Gm = p.Gm + size_t(pair) * N3;
+      const T* Gm = static_cast<const T*>(p.Gm) + size_t(pair) * N3;
       for (int u = tid; u < G::PENCILS; u += NT) {
         const int pp = pencil0 + u;
         CT v[N];
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
 #pragma unroll
         for (int n = 0; n < N; ++n) st2<T>(HA0 + n * N2 + pp, v[n]);
 #pragma unroll
-        for (int n = 0; n < N; ++n) v[n] = scale<T>(ld2<T>(Fj + n * N2 + pp), T(__ldg(Gm + n * N2 + pp)));
+        for (int n = 0; n < N; ++n) v[n] = scale<T>(ld2<T>(Fj + n * N2 + pp), __ldg(Gm + n * N2 + pp));
         fft_line<T, N, +1>(v);
 #pragma unroll
         for (int n = 0; n < N; ++n) st2<T>(HB0 + n * N2 + pp, v[n]);
@@ -642,7 +642,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.ent_w = pl.d_ent_w;
   kp.phase = pl.d_phase;
   kp.Fw = pl.d_Fwf ? static_cast<const void*>(pl.d_Fwf) : static_cast<const void*>(pl.d_Fw);
-  kp.Gm = pl.d_Gm;
+  kp.Gm = pl.d_Gmf ? static_cast<const void*>(pl.d_Gmf) : static_cast<const void*>(pl.d_Gm);
   kp.scratch = pl.d_scratch;
   kp.phase_smem = pl.shape.phase_smem;
   kp.work_counter = pl.d_counter;

@@ -37,7 +37,7 @@ struct KernelParams {
   const void* phase;      // complex: [task][rho][max_ent][role 2][axis 3][N]
   const void* Fw;         // [s*s][n_rho][N^3]: w_rho F^(ij)(k, rho) / N^3, in the plan's real
                           // type (FP32 plans: each FP64 value rounded once)
-  const double* Gm;       // [s*s][N^3]: G^(ij)-(k)
+  const void* Gm;         // [s*s][N^3]: G^(ij)-(k), in the plan's real type
   void* scratch;          // complex: [clusters][SLOT][N^3]
   int phase_smem;         // 1: the task's phase block of the current rho is staged in smem;
                           // 2: only its z phases are
@@ -108,8 +108,9 @@ struct Plan {
   void* d_Qfull = nullptr;         // full operators staged for DGFS_SUM_SPECIES
   double* d_Fw = nullptr;
   double2* d_Fv = nullptr;         // VSS gain weights (complex)
-  float* d_Fwf = nullptr;          // FP32 plans: the gain tables the kernel reads
+  float* d_Fwf = nullptr;          // FP32 plans: the gain and loss tables the kernel reads
   float2* d_Fvf = nullptr;
+  float* d_Gmf = nullptr;
   int* d_ent_m = nullptr;
   int* d_ent_ysh = nullptr;
   double* d_Gm = nullptr;
@@ -154,6 +155,8 @@ int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, in
 // FP32 copies of the gain tables (d_Fwf from d_Fw, or d_Fvf from d_Fv with the halved self
 // pairs' F(sigma) + F(-sigma) pre-added: pair_sum[m] = antipode to add for representative m)
 int launch_gain_tables_f32(Plan& p, const int* d_pair_sum);
+// FP32 copy of an FP64 table (each value rounded once)
+int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps, const int* d_anti);
 

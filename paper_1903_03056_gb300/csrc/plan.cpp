@@ -590,6 +590,12 @@ int upload_plan(Plan& p) {
       if ((rc = dalloc(p, (void**)&p.d_Fwf, nF * sizeof(float)))) return rc;
     }
     if ((rc = launch_gain_tables_f32(p, static_cast<const int*>(d_pair_sum)))) return rc;
+    const size_t nG = size_t(P) * N3;
+    if ((rc = dalloc(p, (void**)&p.d_Gmf, nG * sizeof(float)))) return rc;
+    if ((rc = launch_to_f32(p, p.d_Gm, p.d_Gmf, nG))) return rc;
+    cudaFreeAsync(p.d_Gm, p.home);
+    p.d_Gm = nullptr;
+    total = total - nG * sizeof(double) + nG * sizeof(float);
     if (p.vss) {
       cudaFreeAsync(p.d_Fv, p.home);
       p.d_Fv = nullptr;
@@ -626,7 +632,7 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf};
+                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -658,6 +664,7 @@ void free_plan(Plan& p) {
   p.d_Fv = nullptr;
   p.d_Fwf = nullptr;
   p.d_Fvf = nullptr;
+  p.d_Gmf = nullptr;
   p.d_ent_m = nullptr;
   p.d_ent_ysh = nullptr;
   p.d_counter = nullptr;

@@ -103,6 +103,11 @@ __global__ void vss_to_f32_kernel(const double2* __restrict__ src, float2* __res
 
 }  // namespace
 
+int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n) {
+  gain_to_f32_kernel<<<unsigned(n / 256 + 1 < 8192 ? n / 256 + 1 : 8192), 256, 0, p.home>>>(src, dst, n);
+  return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
+}
+
 int launch_gain_tables_f32(Plan& p, const int* d_pair_sum) {
   const size_t N3 = size_t(p.N) * p.N * p.N;
   const size_t P = size_t(p.s) * p.s;

@@ -62,6 +62,11 @@ extern "C" {
 #define DGFS_CONSERVE 1u    /* project each self pair and each stacked cross pair onto the
                                discrete conservation laws (Eq. consv) with FP64 moment sums */
 #define DGFS_SUM_SPECIES 2u /* return sum_j kappa_ij Q_ij per species (Eq. NMBE right-hand side) */
+#define DGFS_PER_PAIR_R 8u  /* each ordered pair (i, j) gets its own radial truncation
+                               R_ij = 2 S_ij, S_ij the support Eq. domain allows for that pair
+                               alone, with its own N_rho-point rule, instead of the common
+                               R = 2 min S_ij (requires R <= 0 in the description; the (i,j)
+                               and (j,i) products are then not shared) */
 #define DGFS_LOSS_ACCURATE 4u /* radial integral of the loss weight G^- (defined after Eq. GG)
                                  with its own 4 N_rho-point Gauss-Legendre rule on [0, R]
                                  instead of the gain's N_rho nodes (the paper only asks for
@@ -84,7 +89,8 @@ typedef struct {
   int N_rho;               /* Gauss-Legendre points in rho on [0, R], >= 1 */
   double R;                /* radial truncation; <= 0 selects R = 2S with S from Eq. domain */
   int precision;           /* DGFS_FP64 or DGFS_FP32 */
-  unsigned flags;          /* 0 or DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE */
+  unsigned flags;          /* 0 or DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE |
+                              DGFS_PER_PAIR_R */
   int max_batch;           /* largest batch of a host-buffer call or of a DGFS_SUM_SPECIES plan */
   const double* kappa;     /* nullable [s*s]: species-sum weights kappa_ij (e.g. 1/Kn_ij, Eq. Kn);
                               NULL = 1.  Used with DGFS_SUM_SPECIES only. */

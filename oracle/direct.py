@@ -118,8 +118,16 @@ def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
     fh_i = coefficients(f_i, L).reshape(-1)
     fh_j = coefficients(f_j, L).reshape(-1)
 
+    # the pair's radial rule: the common one, or (per-pair truncation) a Gauss-Legendre rule of
+    # the same size on [0, pair_R[i, j]]
+    if prob.pair_R is None:
+        R_ij, rho_q, w_q = prob.R, prob.rho, prob.w_rho
+    else:
+        R_ij = float(prob.pair_R[i, j])
+        x, w = np.polynomial.legendre.leggauss(len(prob.rho))
+        rho_q, w_q = 0.5 * R_ij * (x + 1.0), 0.5 * R_ij * w
     G = np.zeros((n_modes, n_modes), dtype=np.complex128)
-    for rho, w_rho in zip(prob.rho, prob.w_rho):
+    for rho, w_rho in zip(rho_q, w_q):
         for sig, w_sig in zip(prob.sigma, prob.w_sigma):
             F = gain_weight_by_quadrature(K, rho, sig, cj, prob.b[i, j], prob.omega[i, j],
                                           prob.alpha[i, j], L, n_t, n_phi)
@@ -130,9 +138,9 @@ def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
     if prob.loss_rule == "accurate":
         # 4 N_rho Gauss-Legendre nodes on [0, R] for the loss weight's radial integral
         x, w = np.polynomial.legendre.leggauss(4 * len(prob.rho))
-        loss_rho, loss_w = 0.5 * prob.R * (x + 1.0), 0.5 * prob.R * w
+        loss_rho, loss_w = 0.5 * R_ij * (x + 1.0), 0.5 * R_ij * w
     else:
-        loss_rho, loss_w = prob.rho, prob.w_rho
+        loss_rho, loss_w = rho_q, w_q
     Gm = loss_weight_by_quadrature(K, loss_rho, loss_w, prob.b[i, j], prob.omega[i, j],
                                    prob.alpha[i, j], L, n_t, n_phi)
     G -= Gm[None, :]

@@ -54,6 +54,9 @@ class Problem:
     # (4 N_rho Gauss-Legendre nodes on [0, R]); the paper asks for G^- "to high accuracy"
     # without naming a rule
     loss_rule: str = "same"
+    # optional per-pair truncation: pair_R[i, j] = 2 S_ij (Eq. domain for that pair alone) with
+    # its own N_rho-point rule; None = the common R of all pairs (the default reading)
+    pair_R: np.ndarray = None
 
     @property
     def s(self):
@@ -61,7 +64,7 @@ class Problem:
 
 
 def make_problem(N, L, masses, omega, alpha=1.0, M=6, N_rho=None, R=None,
-                 b_override=None, sigma=None, w_sigma=None, loss_rule="same"):
+                 b_override=None, sigma=None, w_sigma=None, loss_rule="same", pair_radius=False):
     """Build the discretisation.  ``omega``/``alpha`` may be scalars or [s, s] arrays."""
     masses = np.asarray(masses, dtype=np.float64)
     s = len(masses)
@@ -83,9 +86,23 @@ def make_problem(N, L, masses, omega, alpha=1.0, M=6, N_rho=None, R=None,
     rho, w_rho = quadrature.gauss_legendre_radial(N_rho, R)
     if loss_rule not in ("same", "accurate"):
         raise ValueError(loss_rule)
+    pair_R = None
+    if pair_radius:
+        pair_R = np.array([[2.0 * kernel.pair_support_radius(L, masses[i], masses[j])
+                            for j in range(s)] for i in range(s)])
     return Problem(N=N, L=float(L), masses=masses, omega=omega, alpha=alpha, b=b,
                    sigma=sigma, w_sigma=w_sigma, rho=rho, w_rho=w_rho, R=float(R),
-                   loss_rule=loss_rule)
+                   loss_rule=loss_rule, pair_R=pair_R)
+
+
+def radial_rule(prob, i, j):
+    """(rho nodes, weights, R) of the pair (i, j): the common rule, or with per-pair
+    truncation a Gauss-Legendre rule of the same size on [0, pair_R[i, j]]."""
+    if prob.pair_R is None:
+        return prob.rho, prob.w_rho, prob.R
+    R = float(prob.pair_R[i, j])
+    rho, w = quadrature.gauss_legendre_radial(len(prob.rho), R)
+    return rho, w, R
 
 
 def velocity_grid(N, L):
@@ -143,21 +160,23 @@ def gain_table(prob, i, j, q, m):
     """F^{(ij)}(k, rho_q, sigma_m) on the mode grid (Eq. GG)."""
     kx, ky, kz = mode_grid(prob.N)
     _, cj = kernel.mass_fractions(prob.masses[i], prob.masses[j])
-    return kernel.gain_weight(kx, ky, kz, prob.rho[q], prob.sigma[m], cj, prob.b[i, j],
+    return kernel.gain_weight(kx, ky, kz, radial_rule(prob, i, j)[0][q], prob.sigma[m], cj, prob.b[i, j],
                               prob.omega[i, j], prob.alpha[i, j], prob.L)
 
 
-def loss_rule_nodes(prob):
-    """Radial nodes and weights of the loss weight's rho integral (see Problem.loss_rule)."""
+def loss_rule_nodes(prob, i=0, j=0):
+    """Radial nodes and weights of the loss weight's rho integral for the pair (i, j) (see
+    Problem.loss_rule and Problem.pair_R)."""
+    rho, w_rho, R = radial_rule(prob, i, j)
     if prob.loss_rule == "accurate":
-        return quadrature.gauss_legendre_radial(4 * len(prob.rho), prob.R)
-    return prob.rho, prob.w_rho
+        return quadrature.gauss_legendre_radial(4 * len(prob.rho), R)
+    return rho, w_rho
 
 
 def loss_table(prob, i, j):
     """G^{(ij)-}(m) on the mode grid."""
     kx, ky, kz = mode_grid(prob.N)
-    rho, w_rho = loss_rule_nodes(prob)
+    rho, w_rho = loss_rule_nodes(prob, i, j)
     return kernel.loss_weight(kx, ky, kz, rho, w_rho, prob.b[i, j],
                               prob.omega[i, j], prob.alpha[i, j], prob.L)
 
@@ -173,7 +192,8 @@ def collision_pair(f_i, f_j, prob, i, j):
     fh_j = dft3(f_j, L)
     kx, ky, kz = mode_grid(prob.N)
     gain_hat = np.zeros(fh_i.shape, dtype=np.complex128)
-    for q, (rho, w_rho) in enumerate(zip(prob.rho, prob.w_rho)):
+    rho_q, w_q, _ = radial_rule(prob, i, j)
+    for q, (rho, w_rho) in enumerate(zip(rho_q, w_q)):
         for m, (sig, w_sig) in enumerate(zip(prob.sigma, prob.w_sigma)):
             k_dot_sigma = kx * sig[0] + ky * sig[1] + kz * sig[2]
             a = idft3(np.exp(1j * np.pi * rho * cj * k_dot_sigma / L) * fh_i, L)

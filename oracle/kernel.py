@@ -25,20 +25,20 @@ def mass_fractions(mi, mj):
     return mi / (mi + mj), mj / (mi + mj)
 
 
-def support_radius(L, masses):
-    """Largest support radius S allowed by the anti-aliasing condition (Eq. domain):
+def pair_support_radius(L, mi, mj):
+    """Largest support radius S_ij the anti-aliasing condition (Eq. domain) allows for the
+    ordered pair (i, j):
 
         2L >= ( max(4 m_j/(m_i+m_j), 2) + sqrt(1 + m_j/m_i) ) S + S
-
-    The velocity grid is shared by all species, so S is the minimum over all ordered
-    pairs (i, j).  The radial truncation is then R = 2S (Sec. 4, item 2).
     """
-    S = np.inf
-    for mi in masses:
-        for mj in masses:
-            _, cj = mass_fractions(mi, mj)
-            S = min(S, 2.0 * L / (max(4.0 * cj, 2.0) + np.sqrt(1.0 + mj / mi) + 1.0))
-    return S
+    _, cj = mass_fractions(mi, mj)
+    return 2.0 * L / (max(4.0 * cj, 2.0) + np.sqrt(1.0 + mj / mi) + 1.0)
+
+
+def support_radius(L, masses):
+    """The velocity grid is shared by all species, so S is the minimum of S_ij over all
+    ordered pairs (i, j).  The radial truncation is then R = 2S (Sec. 4, item 2)."""
+    return min(pair_support_radius(L, mi, mj) for mi in masses for mj in masses)
 
 
 def sinc(x):

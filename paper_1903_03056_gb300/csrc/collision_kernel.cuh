@@ -479,7 +479,9 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
               } else {
                 const double2* Fv = static_cast<const double2*>(p.Fv);
                 const double2* F0 = Fv + fo;
-                const double2* F1 = (o == 0 && tk.out1 < 0 && m1 >= 0)
+                // a halved self pair adds F(-sigma); m1 of a cross pair is its antipode for
+                // the reused (j,i) output, if any
+                const double2* F1 = (o == 0 && tk.i == tk.j && m1 >= 0)
                                         ? Fv + ((size_t(pair) * p.n_rho + q) * p.M + m1) * N3
                                         : nullptr;
 #pragma unroll

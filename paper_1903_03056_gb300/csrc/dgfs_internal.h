@@ -88,6 +88,8 @@ struct Plan {
   unsigned flags = 0;
   int max_batch = 0;
   std::vector<double> mass, omega, alpha, b, sigma, w_sigma, rho, w_rho;
+  std::vector<double> pair_R;            // [s*s] radial truncation of every ordered pair
+  std::vector<double> rho_p, w_rho_p;    // [s*s][N_rho] radial rule of every ordered pair
 
   std::vector<TaskDesc> tasks;
   std::vector<GroupDesc> groups;

@@ -245,7 +245,9 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   if (!(d->L > 0.0) || d->s < 1 || d->s > 8 || !d->mass || !d->omega || !d->alpha) return DGFS_ERR_INVALID_ARG;
   if (d->N_rho < 1 || d->N_rho > 4096 || d->M < 1 || d->max_batch < 0) return DGFS_ERR_INVALID_ARG;
   if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32) return DGFS_ERR_INVALID_ARG;
-  if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE)) != 0u) return DGFS_ERR_INVALID_ARG;
+  if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE | DGFS_PER_PAIR_R)) != 0u)
+    return DGFS_ERR_INVALID_ARG;
+  if ((d->flags & DGFS_PER_PAIR_R) && d->R > 0.0) return DGFS_ERR_INVALID_ARG;
   const int s = d->s;
   p.N = d->N;
   p.L = d->L;
@@ -290,18 +292,17 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   if (d->w_sigma) p.w_sigma.assign(d->w_sigma, d->w_sigma + d->M);
   else p.w_sigma.assign(d->M, 4.0 * kPi / d->M);
   // radial truncation: R = 2S, S the largest support allowed by Eq. domain for every pair
-  if (d->R > 0.0) {
-    p.R = d->R;
-  } else {
-    double S = 1e300;
-    for (int i = 0; i < s; ++i)
-      for (int j = 0; j < s; ++j) {
-        const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
-        const double den = std::max(4.0 * cj, 2.0) + std::sqrt(1.0 + p.mass[j] / p.mass[i]) + 1.0;
-        S = std::min(S, 2.0 * p.L / den);
-      }
-    p.R = 2.0 * S;
-  }
+  // (S_ij for the pair alone, the minimum over the pairs for the common R)
+  std::vector<double> S_pair(size_t(s) * s);
+  double S = 1e300;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
+      const double den = std::max(4.0 * cj, 2.0) + std::sqrt(1.0 + p.mass[j] / p.mass[i]) + 1.0;
+      S_pair[size_t(i) * s + j] = 2.0 * p.L / den;
+      S = std::min(S, S_pair[size_t(i) * s + j]);
+    }
+  p.R = d->R > 0.0 ? d->R : 2.0 * S;
   std::vector<double> x, w;
   gauss_legendre(p.N_rho, x, w);
   p.rho.resize(p.N_rho);
@@ -309,6 +310,17 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   for (int q = 0; q < p.N_rho; ++q) {
     p.rho[q] = 0.5 * p.R * (x[q] + 1.0);
     p.w_rho[q] = 0.5 * p.R * w[q];
+  }
+  const bool per_pair = (p.flags & DGFS_PER_PAIR_R) != 0u;
+  p.pair_R.resize(size_t(s) * s);
+  p.rho_p.resize(size_t(s) * s * p.N_rho);
+  p.w_rho_p.resize(size_t(s) * s * p.N_rho);
+  for (int o = 0; o < s * s; ++o) {
+    p.pair_R[o] = per_pair ? 2.0 * S_pair[o] : p.R;
+    for (int q = 0; q < p.N_rho; ++q) {
+      p.rho_p[size_t(o) * p.N_rho + q] = 0.5 * p.pair_R[o] * (x[q] + 1.0);
+      p.w_rho_p[size_t(o) * p.N_rho + q] = 0.5 * p.pair_R[o] * w[q];
+    }
   }
 
   // antipodal partner of every direction (equal weights required for the pair reuse)
@@ -346,8 +358,10 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   p.ent_m.clear();
   p.ent_ysh.clear();
   p.max_ent = 0;
+  // the (i,j)/(j,i) product reuse needs one radial rule for both pairs
+  const bool reuse = antipodal && !per_pair;
   for (int i = 0; i < s; ++i) {
-    for (int j = antipodal ? i : 0; j < s; ++j) {
+    for (int j = reuse ? i : 0; j < s; ++j) {
       std::vector<std::pair<int, double>> ent;
       for (int m = 0; m < M; ++m) {
         if (antipodal && i == j) {
@@ -370,7 +384,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
       tk.i = i;
       tk.j = j;
       tk.out0 = i * s + j;
-      tk.out1 = (antipodal && i != j) ? j * s + i : -1;
+      tk.out1 = (reuse && i != j) ? j * s + i : -1;
       tk.ent_off = int(p.ent_w.size());
       tk.n_ent = int(ent.size());
       tk.grp_off = int(p.groups.size());
@@ -439,38 +453,35 @@ int upload_plan(Plan& p) {
   if (!p.home && cudaStreamCreateWithFlags(&p.home, cudaStreamNonBlocking) != cudaSuccess) return DGFS_ERR_CUDA;
   if (!p.last_eval && cudaEventCreateWithFlags(&p.last_eval, cudaEventDisableTiming) != cudaSuccess)
     return DGFS_ERR_CUDA;
-  // radial rule of the loss weight: the gain's nodes, or (DGFS_LOSS_ACCURATE) 4 N_rho
-  // Gauss-Legendre nodes of its own on [0, R]
-  std::vector<double> lrho = p.rho, lw = p.w_rho;
-  if (p.flags & DGFS_LOSS_ACCURATE) {
-    std::vector<double> x, w;
-    gauss_legendre(4 * NR, x, w);
-    lrho.resize(x.size());
-    lw.resize(x.size());
-    for (size_t q = 0; q < x.size(); ++q) {
-      lrho[q] = 0.5 * p.R * (x[q] + 1.0);
-      lw[q] = 0.5 * p.R * w[q];
-    }
-  }
-  const int NL = int(lrho.size());
+  // radial rule of the pair (i, j): node q of pair o
+  auto rho_of = [&](int o, int q) { return p.rho_p[size_t(o) * NR + q]; };
+  auto w_rho_of = [&](int o, int q) { return p.w_rho_p[size_t(o) * NR + q]; };
+  // radial rule of the loss weight per pair: the gain's nodes, or (DGFS_LOSS_ACCURATE) 4 N_rho
+  // Gauss-Legendre nodes of its own on [0, R_ij]
+  const bool acc_loss = (p.flags & DGFS_LOSS_ACCURATE) != 0u;
+  const int NL = acc_loss ? 4 * NR : NR;
+  std::vector<double> lx, lwt;
+  if (acc_loss) gauss_legendre(NL, lx, lwt);
   // per (pair, rho) constants of the weight tables: gain prefactor and sinc scale, loss
-  // prefactor; the sinc scale of the loss depends on rho only
-  std::vector<double> fcoef(size_t(P) * NR * 2), gcoef(size_t(P) * NL), gscale(NL);
+  // prefactor and sinc scale
+  std::vector<double> fcoef(size_t(P) * NR * 2), gcoef(size_t(P) * NL), gscale(size_t(P) * NL);
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
       const int o = i * s + j;
       const double b = p.b[o], om = p.omega[o], al = p.alpha[o];
       const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
       for (int q = 0; q < NR; ++q) {
-        const double rp = std::pow(p.rho[q], 4.0 - 2.0 * om);
-        fcoef[2 * (size_t(o) * NR + q)] = p.w_rho[q] * 4.0 * kPi * b * rp / double(N3);
-        fcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
+        const double rp = std::pow(rho_of(o, q), 4.0 - 2.0 * om);
+        fcoef[2 * (size_t(o) * NR + q)] = w_rho_of(o, q) * 4.0 * kPi * b * rp / double(N3);
+        fcoef[2 * (size_t(o) * NR + q) + 1] = kPi * rho_of(o, q) * cj / p.L;
       }
-      for (int q = 0; q < NL; ++q)
-        gcoef[size_t(o) * NL + q] =
-            8.0 * kPi * kPi * std::pow(2.0, al) / al * b * lw[q] * std::pow(lrho[q], 4.0 - 2.0 * om);
+      for (int q = 0; q < NL; ++q) {
+        const double lr = acc_loss ? 0.5 * p.pair_R[o] * (lx[q] + 1.0) : rho_of(o, q);
+        const double lw = acc_loss ? 0.5 * p.pair_R[o] * lwt[q] : w_rho_of(o, q);
+        gcoef[size_t(o) * NL + q] = 8.0 * kPi * kPi * std::pow(2.0, al) / al * b * lw * std::pow(lr, 4.0 - 2.0 * om);
+        gscale[size_t(o) * NL + q] = kPi * lr / p.L;
+      }
     }
-  for (int q = 0; q < NL; ++q) gscale[q] = kPi * lrho[q] / p.L;
   // phase factors exp(i pi shift_d k / L) per task, radial node, entry, role, axis
   const int NT = int(p.tasks.size());
   const size_t nph = size_t(NT) * NR * p.max_ent * 2 * 3 * N;
@@ -482,8 +493,9 @@ int upload_plan(Plan& p) {
     for (int q = 0; q < NR; ++q)
       for (int e = 0; e < tk.n_ent; ++e) {
         const double* sg = &p.sigma[3 * p.ent_sigma[tk.ent_off + e]];
+        const double rq = rho_of(tk.out0, q);
         for (int role = 0; role < 2; ++role) {
-          const double c = role == 0 ? p.rho[q] * cj : -p.rho[q] * ci;
+          const double c = role == 0 ? rq * cj : -rq * ci;
           for (int ax = 0; ax < 3; ++ax) {
             const double sh = c * sg[ax];
             std::complex<double>* dst = &ph[((((size_t(t) * NR + q) * p.max_ent + e) * 2 + role) * 3 + ax) * N];
@@ -538,8 +550,8 @@ int upload_plan(Plan& p) {
         const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
         for (int q = 0; q < NR; ++q) {
           vcoef[2 * (size_t(o) * NR + q)] =
-              p.w_rho[q] * 2.0 * kPi * p.b[o] * std::pow(p.rho[q], 4.0 - 2.0 * p.omega[o]) / double(N3);
-          vcoef[2 * (size_t(o) * NR + q) + 1] = kPi * p.rho[q] * cj / p.L;
+              w_rho_of(o, q) * 2.0 * kPi * p.b[o] * std::pow(rho_of(o, q), 4.0 - 2.0 * p.omega[o]) / double(N3);
+          vcoef[2 * (size_t(o) * NR + q) + 1] = kPi * rho_of(o, q) * cj / p.L;
         }
         std::vector<double> tx, tw;
         gauss_jacobi(n_t, p.alpha[o] - 1.0, tx, tw);

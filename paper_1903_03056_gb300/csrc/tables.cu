@@ -38,7 +38,7 @@ __global__ void loss_table_kernel(double* __restrict__ Gm, size_t count, int N, 
     const size_t o = idx / N3;
     const double ka = kabs_at(idx % N3, N);
     double g = 0.0;
-    for (int q = 0; q < NR; ++q) g += gcoef[o * NR + q] * sinc(gscale[q] * ka);
+    for (int q = 0; q < NR; ++q) g += gcoef[o * NR + q] * sinc(gscale[o * NR + q] * ka);
     Gm[idx] = g;
   }
 }

@@ -29,6 +29,7 @@ DGFS_FP32 = 1
 DGFS_CONSERVE = 1
 DGFS_SUM_SPECIES = 2
 DGFS_LOSS_ACCURATE = 4
+DGFS_PER_PAIR_R = 8
 DGFS_BC_PERIODIC = 0
 DGFS_BC_WALLS = 1
 DGFS_SIDE_WALL = 0

@@ -29,9 +29,10 @@ def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", si
 
 
 def oracle_collision(f, *, N, L, masses, omega, M=12, N_rho=8, sigma=None, w_sigma=None,
-                     b_override=None, R=None, alpha=1.0, loss_rule="same"):
+                     b_override=None, R=None, alpha=1.0, loss_rule="same", pair_radius=False):
     prob = fs.make_problem(N, L, masses, omega=omega, alpha=alpha, M=M, N_rho=N_rho, sigma=sigma,
-                           w_sigma=w_sigma, b_override=b_override, R=R, loss_rule=loss_rule)
+                           w_sigma=w_sigma, b_override=b_override, R=R, loss_rule=loss_rule,
+                           pair_radius=pair_radius)
     return np.stack([fs.collision(fb, prob)[0] for fb in f])
 
 

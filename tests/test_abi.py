@@ -49,7 +49,8 @@ def _desc(**kw):
     (dict(N_rho=0), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(masses=[1.0, -2.0]), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(sigma=[[0.0, 0.0, 2.0]]), dgfs.DGFS_ERR_INVALID_ARG),
-    (dict(flags=8), dgfs.DGFS_ERR_INVALID_ARG),
+    (dict(flags=16), dgfs.DGFS_ERR_INVALID_ARG),
+    (dict(flags=8, R=4.0), dgfs.DGFS_ERR_INVALID_ARG),   # per-pair truncation computes its own R
     (dict(kappa=[1.0, float("nan"), 1.0, 1.0], flags=2), dgfs.DGFS_ERR_INVALID_ARG),
 ])
 def test_invalid_plans_rejected_before_device_work(lib, kw, code):

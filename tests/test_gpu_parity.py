@@ -61,6 +61,21 @@ def test_parity_accurate_loss_rule(precision, alpha):
     assert np.max(np.abs(ref - same)) > 1e-6 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("precision,alpha,flags", [
+    ("fp64", 1.0, 0), ("fp32", 1.0, 0), ("fp64", 1.4, 0), ("fp64", 1.0, "loss")])
+def test_parity_per_pair_radius(precision, alpha, flags):
+    """DGFS_PER_PAIR_R: every ordered pair with its own truncation R_ij = 2 S_ij and its own
+    radial rule, against the oracle's pair_radius=True (VHS, VSS, and with the accurate loss
+    rule)."""
+    N, L, masses, omega, M, N_rho, B = 12, 5.0, (1.0, 3.0), 0.74, 6, 3, 2
+    f = _inputs(N, L, masses, B, seed=512)
+    kw = dict(N=N, L=L, masses=masses, omega=omega, M=M, N_rho=N_rho, alpha=alpha)
+    gflags = dgfs.DGFS_PER_PAIR_R | (dgfs.DGFS_LOSS_ACCURATE if flags == "loss" else 0)
+    Q = gpu_collision(f, precision=precision, flags=gflags, **kw)
+    ref = oracle_collision(f, pair_radius=True, loss_rule="accurate" if flags == "loss" else "same", **kw)
+    assert check(Q, ref, precision)
+
+
 def test_parity_n48_fp32():
     kw = dict(N=48, L=8.0, masses=(1.0, 2.6), omega=0.74, M=6, N_rho=2)
     f = _inputs(48, 8.0, (1.0, 2.6), 1, seed=148)

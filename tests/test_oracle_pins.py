@@ -424,3 +424,37 @@ def test_ssp_rk2_is_second_order_taylor_on_a_linear_equation():
     f = np.array([1.3, -2.0])
     got = homogeneous.ssp_rk2_step(f, dt, lambda x: lam * x)
     assert np.allclose(got, f * (1 + lam * dt + 0.5 * (lam * dt) ** 2), rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- per-pair radial truncation
+
+def test_pair_support_radius_closed_form_and_minimum():
+    """One species: 2L = (3 + sqrt 2) S.  Several: the common S is the minimum of the S_ij."""
+    L = 6.5
+    assert abs(kernel.pair_support_radius(L, 2.0, 2.0) - 2 * L / (3 + np.sqrt(2))) < 1e-14
+    ms = [1.0, 2.0, 4.0]
+    S = [kernel.pair_support_radius(L, a, b) for a in ms for b in ms]
+    assert kernel.support_radius(L, ms) == min(S)
+    assert max(S) > 1.2 * min(S)          # the pairs really differ at this mass ratio
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1.4])
+def test_fast_method_equals_direct_sum_with_per_pair_radius(alpha):
+    prob = fs.make_problem(4, 5.0, [1.0, 3.0], omega=0.74, alpha=alpha, M=6, N_rho=3,
+                           pair_radius=True)
+    assert prob.pair_R[0, 1] != prob.pair_R[1, 0]
+    f = np.random.default_rng(17).random((2, 4, 4, 4))
+    Qf, _ = fs.collision(f, prob)
+    Qd = direct.collision_direct(f, prob)
+    assert np.max(np.abs(Qf - Qd)) < 1e-12 * np.max(np.abs(Qf))
+    common = fs.make_problem(4, 5.0, [1.0, 3.0], omega=0.74, alpha=alpha, M=6, N_rho=3)
+    Qc, _ = fs.collision(f, common)
+    assert np.max(np.abs(Qf - Qc)) > 1e-6 * np.max(np.abs(Qf))
+
+
+def test_per_pair_radius_with_equal_masses_is_the_common_radius():
+    f = np.random.default_rng(18).random((2, 4, 4, 4))
+    a = fs.collision(f, fs.make_problem(4, 5.0, [2.0, 2.0], omega=0.6, M=6, N_rho=3))[0]
+    b = fs.collision(f, fs.make_problem(4, 5.0, [2.0, 2.0], omega=0.6, M=6, N_rho=3,
+                                        pair_radius=True))[0]
+    assert np.max(np.abs(a - b)) < 1e-14 * np.max(np.abs(a))

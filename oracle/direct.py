@@ -15,7 +15,8 @@ integral of G^-).  With enough sphere points the two methods agree to rounding, 
 the fast method's phases, index conventions, normalisations and both weights.
 
 The sum l + m is periodic (mod N) and F is evaluated at the wrapped mode, the reading the
-fast method's FFT convolution implies (listed in the design doc).  A wrapped term l + m = k + pN
+fast method's FFT convolution implies (the paper writes l + m = k without saying how the
+truncated sum treats the modes outside the grid).  A wrapped term l + m = k + pN
 carries the grid's aliasing factor N^-1 sum_n exp(i pi p N v_n / L) per axis, which is
 what the coefficient of a product of grid values contains.
 """

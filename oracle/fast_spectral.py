@@ -17,15 +17,17 @@ Transforms are the plain definition: dense DFT matrices applied along each axis
 (a matrix product per axis; no FFT).  There is no reuse of (i,j)/(j,i) products, no
 antipodal pairing of sigma and no summation over sigma before the forward transform.
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
 
 * grid: cell-centred nodes v_n = -L + (n + 1/2) 2L/N, n = 0..N-1 (with this grid the
   Krook-Wu errors of Table 1 are reproduced; Q at the nodes does not depend on the
   offset once the samples are fixed, only the sample points do);
 * convolutions are periodic (mod N): products of grid values, as the FFT evaluates;
   the gain weight F is evaluated at the wrapped mode k;
-* the radial truncation R = 2S with S from Eq. domain taken over all ordered pairs;
-* G^- uses the same Gauss-Legendre radial rule as the gain term.
+* the radial truncation R = 2S with S from Eq. domain taken over all ordered pairs
+  (optionally per pair: Problem.pair_R);
+* G^- uses the same Gauss-Legendre radial rule as the gain term (optionally a 4 N_rho-point
+  rule of its own: Problem.loss_rule).
 """
 
 from dataclasses import dataclass, field

@@ -95,8 +95,8 @@ def _constraint_rows(N, L, masses, i, j, w):
 def conservation_projection(Q, masses, L, b):
     """Minimal-L2 correction of Q that makes the discrete conservation laws exact:
     Q <- Q - C^T (C C^T)^-1 C Q for every self pair and every stacked cross pair
-    (the post-processing reading listed in the design doc; the paper's fast method itself is not
-    exactly conservative).  Q[s, s, N, N, N]; returns a corrected copy."""
+    (a post-processing step of the kind the paper cites for earlier spectral solvers, not
+    part of its method; the fast method itself is not exactly conservative).  Q[s, s, N, N, N]; returns a corrected copy."""
     Q = np.array(Q, dtype=np.float64, copy=True)
     s, N = Q.shape[0], Q.shape[-1]
     w = 1.0 / np.asarray(b, dtype=np.float64)

@@ -4,7 +4,7 @@
   quadrature approximation of Eq. GG).
 * Sphere: an M-point spherical design with equal weights 4*pi/M (Sec. 4).  The paper
   takes Womersley's designs; their point files are not available here, so the built-in
-  designs are the Platonic-solid designs listed below (readings stated in the design doc):
+  designs are the Platonic-solid designs listed below, in the orientation written here:
 
   - M = 6  : octahedron vertices +-e_d (a spherical 3-design),
   - M = 12 : icosahedron vertices (0, +-1, +-phi) and cyclic permutations (5-design),

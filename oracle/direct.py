@@ -93,8 +93,15 @@ def loss_weight_by_quadrature(kvec, rho_nodes, rho_weights, b, omega, alpha, L, 
     return out
 
 
-def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
-    """Q^(ij) on the grid from the direct sum (Eq. sum); returns complex grid values."""
+def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64, truncation="periodic"):
+    """Q^(ij) on the grid from the direct sum (Eq. sum); returns complex grid values.
+
+    truncation="periodic": l + m taken modulo N (what the fast method evaluates);
+    truncation="literal": only pairs with l + m inside the grid's mode range contribute and
+    no term wraps -- the truncated sum read literally.  The difference of the two is the
+    aliasing diagnostic of the periodic reading."""
+    if truncation not in ("periodic", "literal"):
+        raise ValueError(truncation)
     N, L = prob.N, prob.L
     mi, mj = prob.masses[i], prob.masses[j]
     ci, cj = mi / (mi + mj), mj / (mi + mj)
@@ -146,6 +153,8 @@ def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
                                    prob.alpha[i, j], L, n_t, n_phi)
     G -= Gm[None, :]
     terms = alias * G * fh_i[:, None] * fh_j[None, :]
+    if truncation == "literal":
+        terms = np.where(np.all(p3 == 0, axis=-1), G * fh_i[:, None] * fh_j[None, :], 0.0)
     Qh = (np.bincount(wrap.reshape(-1), weights=terms.real.reshape(-1), minlength=n_modes)
           + 1j * np.bincount(wrap.reshape(-1), weights=terms.imag.reshape(-1),
                              minlength=n_modes))
@@ -153,7 +162,8 @@ def collision_pair_direct(f_i, f_j, prob, i, j, n_t=40, n_phi=64):
 
 
 def collision_direct(f, prob, **kw):
-    """All s^2 operators by the direct method: f[s, N, N, N] -> Q[s, s, N, N, N] (real part)."""
+    """All s^2 operators by the direct method: f[s, N, N, N] -> Q[s, s, N, N, N] (real part).
+    Keyword arguments go to collision_pair_direct (e.g. truncation="literal")."""
     s = f.shape[0]
     N = prob.N
     Q = np.zeros((s, s, N, N, N))

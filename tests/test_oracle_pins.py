@@ -458,3 +458,39 @@ def test_per_pair_radius_with_equal_masses_is_the_common_radius():
     b = fs.collision(f, fs.make_problem(4, 5.0, [2.0, 2.0], omega=0.6, M=6, N_rho=3,
                                         pair_radius=True))[0]
     assert np.max(np.abs(a - b)) < 1e-14 * np.max(np.abs(a))
+
+
+# ---------------------------------------------------------------- aliasing diagnostic
+
+def test_literal_and_periodic_sums_agree_for_band_limited_states():
+    """With f_hat nonzero only for |k_d| <= N/4 - 1, every l + m stays inside the mode range,
+    so the literal truncated sum and the periodic one are the same sum."""
+    N, L = 8, 5.0
+    prob = fs.make_problem(N, L, [1.0, 2.0], omega=0.6, M=6, N_rho=2)
+    rng = np.random.default_rng(21)
+    k = fs.modes(N)
+    keep = np.abs(k) <= N // 4 - 1
+    mask = keep[:, None, None] & keep[None, :, None] & keep[None, None, :]
+    fs_ = []
+    for _ in range(2):
+        c = (rng.normal(size=(N, N, N)) + 1j * rng.normal(size=(N, N, N))) * mask
+        fs_.append(fs.idft3(c, L))
+    a = direct.collision_pair_direct(fs_[0], fs_[1], prob, 0, 1, n_t=8, n_phi=16)
+    b = direct.collision_pair_direct(fs_[0], fs_[1], prob, 0, 1, n_t=8, n_phi=16, truncation="literal")
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+
+
+def test_aliasing_diagnostic_shrinks_as_the_grid_resolves_the_state():
+    """The periodic reading differs from the literal truncated sum only through wrapped terms;
+    for a fixed Maxwellian-mixture state the difference falls as N grows (measured 1.43 at
+    N = 8, 0.17 at N = 12, relative to max |Q|)."""
+    from paper_1903_03056_gb300 import synth
+    diag = []
+    for N in (8, 12):
+        w = synth.Workload("alias", 1, N, 5.0, (1.0, 2.0), 0.5, 1.0, 6, 3, "bimaxwellian", 0.0, 7)
+        f = synth.batch_distribution(w)[0][0]
+        prob = fs.make_problem(N, 5.0, [1.0], omega=0.5, M=6, N_rho=3)
+        p = direct.collision_pair_direct(f, f, prob, 0, 0, n_t=8, n_phi=16)
+        q = direct.collision_pair_direct(f, f, prob, 0, 0, n_t=8, n_phi=16, truncation="literal")
+        diag.append(np.max(np.abs(p - q)) / np.max(np.abs(p)))
+    assert diag[1] < diag[0] / 5

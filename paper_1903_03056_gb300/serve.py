@@ -219,102 +219,98 @@ class ServingEngine:
                      mean_latency=sum(lat) / len(lat), peak_bytes=peak_bytes,
                      peak_inflight=peak_inflight, budget=self.budget)
 
+    def _run_chunked(self, requests, poll_s):
+        """Chunked loop (see the module docstring); returns Stats."""
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        arrivals = collections.deque(reqs)
+        pending = collections.deque()       # arrived, waiting for admission (FIFO)
+        plans = {}                          # rid -> future of the plan
+        active = []                         # admitted, nodes left to submit or running
+        running = {}                        # slot -> (request, lo, hi)
+        free_slots = list(range(self.slots))
+        in_use = 0
+        peak_bytes, peak_inflight = 0, 0
+        builder = ThreadPoolExecutor(max_workers=2)
+        t0 = time.perf_counter()
 
-def _chunked_engine_run(self, requests, poll_s):
-    """Chunked loop (see the module docstring); returns Stats."""
-    reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
-    arrivals = collections.deque(reqs)
-    pending = collections.deque()       # arrived, waiting for admission (FIFO)
-    plans = {}                          # rid -> future of the plan
-    active = []                         # admitted, nodes left to submit or running
-    running = {}                        # slot -> (request, lo, hi)
-    free_slots = list(range(self.slots))
-    in_use = 0
-    peak_bytes, peak_inflight = 0, 0
-    builder = ThreadPoolExecutor(max_workers=2)
-    t0 = time.perf_counter()
+        def pick():
+            # one chunk per plan at a time: a plan's evaluations share its workspace and the library
+            # serialises them, so a second chunk of the same plan would only hold a slot
+            busy = {r.plan_key for (r, _, _) in running.values()}
+            cand = [r for r in active if r.next_node < r.batch and r.plan_key not in busy]
+            if not cand:
+                return None
+            if self.policy == "fifo":
+                return min(cand, key=lambda r: (r.arrival, r.rid))
+            return min(cand, key=lambda r: ((r.batch - r.next_node) * cost_per_node(r), r.arrival, r.rid))
 
-    def pick():
-        # one chunk per plan at a time: a plan's evaluations share its workspace and the library
-        # serialises them, so a second chunk of the same plan would only hold a slot
-        busy = {r.plan_key for (r, _, _) in running.values()}
-        cand = [r for r in active if r.next_node < r.batch and r.plan_key not in busy]
-        if not cand:
-            return None
-        if self.policy == "fifo":
-            return min(cand, key=lambda r: (r.arrival, r.rid))
-        return min(cand, key=lambda r: ((r.batch - r.next_node) * cost_per_node(r), r.arrival, r.rid))
-
-    try:
-        while arrivals or pending or active:
-            now = time.perf_counter() - t0
-            while arrivals and arrivals[0].arrival <= now:
-                pending.append(arrivals.popleft())
-            for r in list(pending)[: self.prefetch]:
-                if r.rid not in plans:
-                    plans[r.rid] = builder.submit(self.ex.prepare, r)
-            # admission in arrival order under the memory budget (no slot needed)
-            while pending:
-                r = pending[0]
-                fut = plans.get(r.rid)
-                if fut is None or not fut.done():
-                    break
-                need = fut.result()
-                if need > self.budget:
-                    raise RuntimeError("request %d needs %d bytes, budget %d" % (r.rid, need, self.budget))
-                if in_use + need > self.budget:
-                    break
-                pending.popleft()
-                r.bytes = need
-                r.admitted = time.perf_counter() - t0
-                r.next_node, r.nodes_done = 0, 0
-                in_use += need
-                self.ex.begin(r)
-                active.append(r)
-                peak_bytes = max(peak_bytes, in_use)
-            # fill free slots with chunks
-            while free_slots:
-                r = pick()
-                if r is None:
-                    break
-                n = max(1, int(self.chunk_s / cost_per_node(r)))
-                lo, hi = r.next_node, min(r.batch, r.next_node + n)
-                r.next_node = hi
-                slot = free_slots.pop()
-                self.ex.submit_chunk(r, slot, lo, hi)
-                running[slot] = (r, lo, hi)
-                peak_inflight = max(peak_inflight, len(running))
-            # chunk completions
-            for slot, (r, lo, hi) in list(running.items()):
-                if self.ex.chunk_done(slot):
-                    del running[slot]
-                    free_slots.append(slot)
-                    r.nodes_done += hi - lo
-                    if r.nodes_done == r.batch:
-                        r.done = time.perf_counter() - t0
-                        self.ex.finish(r)
-                        plans.pop(r.rid, None)
-                        in_use -= r.bytes
-                        active.remove(r)
-            if not running and not pending and not active and arrivals:
-                wait = arrivals[0].arrival - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
-            else:
-                time.sleep(poll_s)
-    finally:
-        builder.shutdown(wait=True)
-    lat = [r.latency for r in reqs]
-    first = min(r.arrival for r in reqs)
-    makespan = max(r.done for r in reqs) - first
-    return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=makespan,
-                 p50=percentile(lat, 50), p99=percentile(lat, 99),
-                 mean_latency=sum(lat) / len(lat), peak_bytes=peak_bytes,
-                 peak_inflight=peak_inflight, budget=self.budget,
-                 extra={"policy": self.policy, "chunk_s": self.chunk_s})
-
-
-ServingEngine._run_chunked = _chunked_engine_run
+        try:
+            while arrivals or pending or active:
+                now = time.perf_counter() - t0
+                while arrivals and arrivals[0].arrival <= now:
+                    pending.append(arrivals.popleft())
+                for r in list(pending)[: self.prefetch]:
+                    if r.rid not in plans:
+                        plans[r.rid] = builder.submit(self.ex.prepare, r)
+                # admission in arrival order under the memory budget (no slot needed)
+                while pending:
+                    r = pending[0]
+                    fut = plans.get(r.rid)
+                    if fut is None or not fut.done():
+                        break
+                    need = fut.result()
+                    if need > self.budget:
+                        raise RuntimeError("request %d needs %d bytes, budget %d" % (r.rid, need, self.budget))
+                    if in_use + need > self.budget:
+                        break
+                    pending.popleft()
+                    r.bytes = need
+                    r.admitted = time.perf_counter() - t0
+                    r.next_node, r.nodes_done = 0, 0
+                    in_use += need
+                    self.ex.begin(r)
+                    active.append(r)
+                    peak_bytes = max(peak_bytes, in_use)
+                # fill free slots with chunks
+                while free_slots:
+                    r = pick()
+                    if r is None:
+                        break
+                    n = max(1, int(self.chunk_s / cost_per_node(r)))
+                    lo, hi = r.next_node, min(r.batch, r.next_node + n)
+                    r.next_node = hi
+                    slot = free_slots.pop()
+                    self.ex.submit_chunk(r, slot, lo, hi)
+                    running[slot] = (r, lo, hi)
+                    peak_inflight = max(peak_inflight, len(running))
+                # chunk completions
+                for slot, (r, lo, hi) in list(running.items()):
+                    if self.ex.chunk_done(slot):
+                        del running[slot]
+                        free_slots.append(slot)
+                        r.nodes_done += hi - lo
+                        if r.nodes_done == r.batch:
+                            r.done = time.perf_counter() - t0
+                            self.ex.finish(r)
+                            plans.pop(r.rid, None)
+                            in_use -= r.bytes
+                            active.remove(r)
+                if not running and not pending and not active and arrivals:
+                    wait = arrivals[0].arrival - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                else:
+                    time.sleep(poll_s)
+        finally:
+            builder.shutdown(wait=True)
+        lat = [r.latency for r in reqs]
+        first = min(r.arrival for r in reqs)
+        makespan = max(r.done for r in reqs) - first
+        return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=makespan,
+                     p50=percentile(lat, 50), p99=percentile(lat, 99),
+                     mean_latency=sum(lat) / len(lat), peak_bytes=peak_bytes,
+                     peak_inflight=peak_inflight, budget=self.budget,
+                     extra={"policy": self.policy, "chunk_s": self.chunk_s})
 
 
 class FakeExecutor:

@@ -48,8 +48,10 @@ struct Geo {
   static constexpr int N2 = N * N;
   static constexpr int N3 = N * N * N;
   static constexpr int PITCH = N + 1;  // padded smem row (complex elements)
-  // P accumulates in registers when a second line of N complex values still fits
-  static constexpr bool PREG = (sizeof(T) == 4 && N <= 32) || N <= 16;
+  // P accumulates in registers when a second line of N complex values still fits (FP32 up to
+  // N = 48: ~50 bytes of spills there, and one plane buffer per group less; measured 8-10 %
+  // faster than P in shared memory at N = 48)
+  static constexpr bool PREG = (sizeof(T) == 4 && N <= 48) || N <= 16;
   static constexpr int CL = Shape<T, N>::cluster;
   static constexpr int GP = Shape<T, N>::groups;
   static constexpr int MINB = Shape<T, N>::min_blocks;  // CTAs per SM the registers are sized for

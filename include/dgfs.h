@@ -81,7 +81,9 @@ typedef struct {
   int s;                   /* number of species, 1..8 */
   const double* mass;      /* [s] nondimensional masses m_i / m_0 (Sec. 3), > 0 */
   const double* omega;     /* [s*s] row-major (i, j): viscosity index omega_ij in [0.5, 1] */
-  const double* alpha;     /* [s*s]: scattering parameter alpha_ij; this build needs 1 (VHS) */
+  const double* alpha;     /* [s*s]: VSS scattering parameter alpha_ij in [1, 2]; 1 = VHS.  Any
+                              alpha != 1 selects the sigma-dependent complex gain table
+                              [s*s][N_rho][M][N^3] (memory grows by the factor 2 M) */
   const double* b_override;/* nullable [s*s]: kernel prefactor b_ij replacing Eq. NVSS */
   int M;                   /* sphere points; with sigma == NULL one of 6, 12, 32 */
   const double* sigma;     /* nullable [M*3]: unit directions of the sphere rule */

@@ -99,9 +99,9 @@ typedef struct {
 } dgfs_plan_desc;
 
 /* Build the tables (Gauss-Legendre rule, design, b_ij of Eq. NVSS, R of Eq. domain, gain
- * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), all FP64, the N^3-sized
- * ones computed on the device) and the workspace on the current device.  *out receives the
- * plan.  Device memory is allocated stream-ordered on a stream the plan owns; the call
+ * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), computed in FP64, the
+ * N^3-sized ones on the device; a DGFS_FP32 plan keeps them rounded once to FP32) and the
+ * workspace on the current device.  *out receives the plan.  Device memory is allocated stream-ordered on a stream the plan owns; the call
  * returns when the plan is ready and never synchronises other streams. */
 int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out);
 
@@ -111,8 +111,9 @@ int dgfs_destroy_plan(dgfs_plan plan);
 
 /* Q = all s^2 collision operators of the batch (Sec. 4), device pointers, stream-ordered.
  * f_dev: [batch][s][N][N][N], Q_dev: [batch][s][s][N][N][N], element type per precision,
- * both 16-byte aligned.  batch >= 0 (0 is a no-op).  Calls on one plan must not overlap
- * in time on the device (the workspace is shared); they do not when issued on one stream.
+ * both 16-byte aligned.  batch >= 0 (0 is a no-op).  Calls on one plan share its workspace:
+ * the library orders a call issued on another stream after the plan's previous one (see
+ * Threads above).
  * With DGFS_CONSERVE every self pair Q_ii and every stacked cross pair [Q_ij; Q_ji] is
  * replaced by its nearest (L2) vector satisfying the discrete laws of Eq. consv: mass of each
  * operator, and m_i w_ij int v Q_ij + m_j w_ji int v Q_ji = 0 and the same with |v|^2, with
@@ -135,7 +136,8 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
  * for `batch` nodes). */
 int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace);
 
-/* The radial truncation R the plan uses (R = 2S from Eq. domain unless given). */
+/* The radial truncation R the plan uses (R = 2S from Eq. domain unless given; with
+ * DGFS_PER_PAIR_R the common R, the pairs using their own R_ij = 2 S_ij >= R). */
 int dgfs_plan_radius(dgfs_plan plan, double* R);
 
 /* One step of the second-order strong-stability-preserving Runge-Kutta scheme (the time
@@ -148,8 +150,8 @@ int dgfs_plan_radius(dgfs_plan plan, double* R);
 int dgfs_ssp_rk2_step(dgfs_plan plan, void* f_dev, double dt, int batch, void* stream);
 
 /* Limit one launch of the persistent collision kernel to a fraction 0 < share <= 1 of the
- * thread-block clusters the device holds (default 1).  Concurrent evaluations on different
- * streams then share the SMs instead of queueing behind one another (serving). */
+ * thread-block clusters the device holds (default 1).  Evaluations of different plans on
+ * different streams then share the SMs instead of queueing behind one another (serving). */
 int dgfs_plan_set_sm_share(dgfs_plan plan, double share);
 
 /* Kernels enqueued by the most recent evaluation on this plan. */

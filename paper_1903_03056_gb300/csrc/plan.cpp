@@ -526,16 +526,29 @@ int upload_plan(Plan& p) {
   int rc;
   void *d_fcoef = nullptr, *d_gcoef = nullptr, *d_gscale = nullptr;
   size_t tmp = 0;
+  // coefficient arrays the table kernels read: freed (stream-ordered) when this function
+  // returns, on every path
+  struct TempBuffers {
+    cudaStream_t st;
+    std::vector<void*> v;
+    ~TempBuffers() {
+      for (void* t : v)
+        if (t) cudaFreeAsync(t, st);
+    }
+  } temps{p.home, {}};
+  auto up_tmp = [&](const auto* host, size_t count, void** d) {
+    const int r = upload(p, host, count, d, tmp);
+    if (*d) temps.v.push_back(*d);
+    return r;
+  };
   if ((rc = dalloc(p, (void**)&p.d_Gm, size_t(P) * N3 * sizeof(double)))) return rc;
   total += size_t(P) * N3 * sizeof(double);
-  if ((rc = upload(p, gcoef.data(), gcoef.size(), &d_gcoef, tmp))) return rc;
-  if ((rc = upload(p, gscale.data(), gscale.size(), &d_gscale, tmp))) return rc;
-  std::vector<void*> tmps = {d_gcoef, d_gscale};
+  if ((rc = up_tmp(gcoef.data(), gcoef.size(), &d_gcoef))) return rc;
+  if ((rc = up_tmp(gscale.data(), gscale.size(), &d_gscale))) return rc;
   if (!p.vss) {
     if ((rc = dalloc(p, (void**)&p.d_Fw, size_t(P) * NR * N3 * sizeof(double)))) return rc;
     total += size_t(P) * NR * N3 * sizeof(double);
-    if ((rc = upload(p, fcoef.data(), fcoef.size(), &d_fcoef, tmp))) return rc;
-    tmps.push_back(d_fcoef);
+    if ((rc = up_tmp(fcoef.data(), fcoef.size(), &d_fcoef))) return rc;
     if ((rc = launch_vhs_tables(p, static_cast<double*>(d_fcoef), static_cast<double*>(d_gcoef),
                                 static_cast<double*>(d_gscale), NL)))
       return rc;
@@ -567,12 +580,11 @@ int upload_plan(Plan& p) {
     void *d_vc = nullptr, *d_gj = nullptr, *d_sg = nullptr, *d_reps = nullptr, *d_anti = nullptr;
     if ((rc = dalloc(p, (void**)&p.d_Fv, size_t(P) * NR * p.M * N3 * sizeof(double2)))) return rc;
     total += size_t(P) * NR * p.M * N3 * sizeof(double2);
-    if ((rc = upload(p, vcoef.data(), vcoef.size(), &d_vc, tmp))) return rc;
-    if ((rc = upload(p, gj.data(), gj.size(), &d_gj, tmp))) return rc;
-    if ((rc = upload(p, p.sigma.data(), p.sigma.size(), &d_sg, tmp))) return rc;
-    if ((rc = upload(p, reps.data(), reps.size(), &d_reps, tmp))) return rc;
-    if ((rc = upload(p, p.anti.data(), p.anti.size(), &d_anti, tmp))) return rc;
-    tmps.insert(tmps.end(), {d_vc, d_gj, d_sg, d_reps, d_anti});
+    if ((rc = up_tmp(vcoef.data(), vcoef.size(), &d_vc))) return rc;
+    if ((rc = up_tmp(gj.data(), gj.size(), &d_gj))) return rc;
+    if ((rc = up_tmp(p.sigma.data(), p.sigma.size(), &d_sg))) return rc;
+    if ((rc = up_tmp(reps.data(), reps.size(), &d_reps))) return rc;
+    if ((rc = up_tmp(p.anti.data(), p.anti.size(), &d_anti))) return rc;
     if ((rc = launch_vss_tables(p, static_cast<double*>(d_vc), static_cast<double*>(d_gj), n_t,
                                 static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()),
                                 static_cast<int*>(d_anti))))
@@ -595,8 +607,7 @@ int upload_plan(Plan& p) {
             const int m0 = p.ent_m[2 * (tk.ent_off + e)], m1 = p.ent_m[2 * (tk.ent_off + e) + 1];
             if (m1 >= 0) pair_sum[m0] = m1;
           }
-      if ((rc = upload(p, pair_sum.data(), pair_sum.size(), &d_pair_sum, tmp))) return rc;
-      tmps.push_back(d_pair_sum);
+      if ((rc = up_tmp(pair_sum.data(), pair_sum.size(), &d_pair_sum))) return rc;
       if ((rc = dalloc(p, (void**)&p.d_Fvf, nF * sizeof(float2)))) return rc;
     } else {
       if ((rc = dalloc(p, (void**)&p.d_Fwf, nF * sizeof(float)))) return rc;
@@ -618,7 +629,6 @@ int upload_plan(Plan& p) {
       total = total - nF * sizeof(double) + nF * sizeof(float);
     }
   }
-  for (void* t : tmps) cudaFreeAsync(t, p.home);
   if ((rc = upload(p, p.ent_w.data(), p.ent_w.size(), (void**)&p.d_ent_w, total))) return rc;
   if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
   if ((rc = upload(p, p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;

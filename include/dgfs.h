@@ -83,7 +83,9 @@ typedef struct {
   const double* omega;     /* [s*s] row-major (i, j): viscosity index omega_ij in [0.5, 1] */
   const double* alpha;     /* [s*s]: VSS scattering parameter alpha_ij in [1, 2]; 1 = VHS.  Any
                               alpha != 1 selects the sigma-dependent complex gain table
-                              [s*s][N_rho][M][N^3] (memory grows by the factor 2 M) */
+                              [s*s][N_rho][slots][N^3], one slot per direction without an
+                              antipode and per antipodal pair (M / 2 slots for an antipodal
+                              rule, since F(-sigma) = conj F(sigma)) */
   const double* b_override;/* nullable [s*s]: kernel prefactor b_ij replacing Eq. NVSS */
   int M;                   /* sphere points; with sigma == NULL one of 6, 12, 32 */
   const double* sigma;     /* nullable [M*3]: unit directions of the sphere rule */

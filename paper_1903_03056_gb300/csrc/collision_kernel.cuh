@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
           // for a halved self pair F(sigma) + F(-sigma), for the reused (j,i) pair F^(ji)(-sigma)
           const int e = k - 2;
           const CT* const PVr = (e & 1) ? PV1 : PV;
-          const int m0 = p.ent_m[2 * (tk.ent_off + e)], m1 = p.ent_m[2 * (tk.ent_off + e) + 1];
+          const int c0 = p.ent_m[2 * (tk.ent_off + e)], c1 = p.ent_m[2 * (tk.ent_off + e) + 1];
+          const bool self_sum = tk.i == tk.j && c1 >= 0;
           const bool first = q == 0 && e == 0;
           for (int u = tid; u < G::PENCILS; u += NT) {
             const int pp = pencil0 + u;
@@ -467,33 +468,29 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             for (int o = 0; o < 2; ++o) {
               const int pair = o == 0 ? tk.out0 : tk.out1;
               if (pair < 0) break;
-              const size_t fo = ((size_t(pair) * p.n_rho + q) * p.M + (o == 0 ? m0 : m1)) * N3;
+              // slot code of this output's direction: 2 slot + 1 when the slot holds the
+              // antipode's weight (read conjugated)
+              const int code = o == 0 ? c0 : c1;
+              const size_t fo = ((size_t(pair) * p.n_rho + q) * p.n_fslot + (code >> 1)) * N3;
+              const T sgn = (code & 1) ? T(-1) : T(1);
               CT* acc = o == 0 ? QA : QB;
               if constexpr (sizeof(T) == 4) {
-                // FP32 table; a halved self pair's slot already holds F(sigma) + F(-sigma)
+                // FP32 table; a self pair's slot already holds F(sigma) + F(-sigma)
                 const float2* F0 = static_cast<const float2*>(p.Fv) + fo;
 #pragma unroll
                 for (int n = 0; n < N; ++n) {
-                  CT val = cmul<T>(v[n], __ldg(F0 + n * N2 + pp));
+                  const float2 fw = __ldg(F0 + n * N2 + pp);
+                  CT val = cmul<T>(v[n], mk<T>(fw.x, sgn * fw.y));
                   if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
                   st2<T>(acc + n * N2 + pp, val);
                 }
               } else {
-                const double2* Fv = static_cast<const double2*>(p.Fv);
-                const double2* F0 = Fv + fo;
-                // a halved self pair adds F(-sigma); m1 of a cross pair is its antipode for
-                // the reused (j,i) output, if any
-                const double2* F1 = (o == 0 && tk.i == tk.j && m1 >= 0)
-                                        ? Fv + ((size_t(pair) * p.n_rho + q) * p.M + m1) * N3
-                                        : nullptr;
+                const double2* F0 = static_cast<const double2*>(p.Fv) + fo;
 #pragma unroll
                 for (int n = 0; n < N; ++n) {
                   double2 fw = __ldg(F0 + n * N2 + pp);
-                  if (F1) {
-                    const double2 f1 = __ldg(F1 + n * N2 + pp);
-                    fw.x += f1.x;
-                    fw.y += f1.y;
-                  }
+                  // a halved self pair takes F(sigma) + F(-sigma) = F + conj F
+                  fw = self_sum ? make_double2(fw.x + fw.x, 0.0) : make_double2(fw.x, sgn * fw.y);
                   CT val = cmul<T>(v[n], mk<T>(T(fw.x), T(fw.y)));
                   if (!first) val = add<T>(val, ld2<T>(acc + n * N2 + pp));
                   st2<T>(acc + n * N2 + pp, val);
@@ -651,7 +648,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.phase_smem = pl.shape.phase_smem;
   kp.work_counter = pl.d_counter;
   kp.vss = pl.vss ? 1 : 0;
-  kp.M = pl.M;
+  kp.n_fslot = pl.n_fslot;
   kp.Fv = pl.d_Fvf ? static_cast<const void*>(pl.d_Fvf) : static_cast<const void*>(pl.d_Fv);
   kp.ent_m = pl.d_ent_m;
   kp.ent_ysh = pl.d_ent_ysh;

@@ -44,11 +44,15 @@ struct KernelParams {
   unsigned* work_counter; // next work item (reset to 0 before every launch)
   // VSS (alpha != 1): sigma-dependent complex gain weights, one forward transform per entry
   int vss;
-  int M;
-  const void* Fv;         // [s*s][n_rho][M][N^3]: w_rho F^(ij)(k, rho, sigma_m) / N^3, complex
-                          // in the plan's real type; in FP32 plans the slot of a halved self
-                          // pair's representative holds F(sigma) + F(-sigma) (summed in FP64)
-  const int* ent_m;       // [entries][2]: design index of the entry and of its antipode (-1)
+  int n_fslot;            // table slots per (pair, rho): M, or M / 2 with an antipodal design
+  const void* Fv;         // [s*s][n_rho][n_fslot][N^3]: w_rho F^(ij)(k, rho, sigma) / N^3,
+                          // complex in the plan's real type; with an antipodal design a slot
+                          // holds the direction of lower index, its antipode reads it
+                          // conjugated, and in FP32 plans a self pair's slots hold
+                          // F(sigma) + F(-sigma) = 2 Re F(sigma) (summed in FP64)
+  const int* ent_m;       // [entries][2]: slot code (2 slot + conjugation bit) of the entry's
+                          // direction and of its antipode (-1: none); a self pair's entry with
+                          // an antipode takes F(sigma) + F(-sigma)
   const int* ent_ysh;     // [entries]: 1 when the entry has the previous entry's sigma_x and
                           // sigma_y (same group), so both its shifted volumes share that
                           // entry's x and y passes
@@ -95,7 +99,10 @@ struct Plan {
   std::vector<GroupDesc> groups;
   std::vector<double> ent_w;
   std::vector<int> ent_sigma;   // design index of each entry
-  std::vector<int> ent_m;       // [entries][2] design index and antipode (VSS)
+  std::vector<int> ent_m;       // [entries][2] VSS table slot codes of the entry and its antipode
+  std::vector<int> fslot;       // [M] VSS table slot code of each direction: 2 slot + conj bit
+  int n_fslot = 0;              // slots per (pair, rho) of the VSS table
+  bool antipodal = false;       // every direction has an antipode of equal weight
   std::vector<int> ent_ysh;     // [entries] shares the previous entry's y pass
   std::vector<int> anti;        // antipode of every design direction, -1 if none
   int max_ent = 0;
@@ -154,13 +161,13 @@ int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st
 // on-device FP64 weight tables on the plan's stream (tables.cu)
 int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale, int n_loss);
 int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, int n_loss);
-// FP32 copies of the gain tables (d_Fwf from d_Fw, or d_Fvf from d_Fv with the halved self
-// pairs' F(sigma) + F(-sigma) pre-added: pair_sum[m] = antipode to add for representative m)
-int launch_gain_tables_f32(Plan& p, const int* d_pair_sum);
+// FP32 copies of the gain tables (d_Fwf from d_Fw, or d_Fvf from d_Fv; self_sum: the self
+// pairs' slots take F(sigma) + conj F(sigma), the sum their halved entries read)
+int launch_gain_tables_f32(Plan& p, int self_sum);
 // FP32 copy of an FP64 table (each value rounded once)
 int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
-                      const int* d_reps, int n_reps, const int* d_anti);
+                      const int* d_reps, int n_reps);
 
 // SSP-RK2 stage combinations (stepper.cu): stage 1 f1 = f + dt r; stage 2 f = (f + f1 + dt r)/2
 int launch_rk_stage(const Plan& p, int stage, void* f, void* f1, const void* r, double dt, size_t n, cudaStream_t st);

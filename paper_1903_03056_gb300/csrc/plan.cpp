@@ -340,6 +340,22 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     if (anti[m] < 0) antipodal = false;
   }
   p.anti = antipodal ? anti : std::vector<int>(M, -1);
+  p.antipodal = antipodal;
+  // slots of the VSS gain table: F(k, rho, -sigma) = conj F(k, rho, sigma) (the sphere
+  // integral of Eq. GG with the plane wave's sign flipped), so a direction whose negation owns
+  // a slot at a lower index reads that slot conjugated; every other direction owns a slot
+  p.fslot.assign(M, -1);
+  p.n_fslot = 0;
+  for (int m = 0; m < M; ++m) {
+    const double* a = &p.sigma[3 * m];
+    for (int r = 0; r < m && p.fslot[m] < 0; ++r) {
+      const double* c = &p.sigma[3 * r];
+      if (!(p.fslot[r] & 1) && std::fabs(a[0] + c[0]) < 1e-12 && std::fabs(a[1] + c[1]) < 1e-12 &&
+          std::fabs(a[2] + c[2]) < 1e-12)
+        p.fslot[m] = p.fslot[r] | 1;
+    }
+    if (p.fslot[m] < 0) p.fslot[m] = 2 * p.n_fslot++;
+  }
   auto positive = [&](int m) {
     const double* a = &p.sigma[3 * m];
     for (int dd = 0; dd < 3; ++dd) {
@@ -403,8 +419,11 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
         const auto& e = ent[k];
         p.ent_w.push_back(e.second);
         p.ent_sigma.push_back(e.first);
-        p.ent_m.push_back(e.first);
-        p.ent_m.push_back(antipodal ? anti[e.first] : -1);
+        // a halved self pair reads F(sigma) + F(-sigma) = 2 Re F(sigma): slot without the
+        // conjugation bit, plus the antipode's code as the marker of the sum
+        const bool halved = antipodal && i == j;
+        p.ent_m.push_back(halved ? (p.fslot[e.first] & ~1) : p.fslot[e.first]);
+        p.ent_m.push_back(antipodal ? p.fslot[anti[e.first]] : -1);
         bool ysh = false;
         if (k > 0 && !p.vss) {
           const double* u = &p.sigma[3 * ent[k - 1].first];
@@ -574,20 +593,19 @@ int upload_plan(Plan& p) {
           gj[size_t(o) * 3 * n_t + 2 * n_t + k] = std::sqrt(std::max(0.0, 1.0 - tx[k] * tx[k]));
         }
       }
+    // the direction that owns each slot
     std::vector<int> reps;
     for (int m = 0; m < p.M; ++m)
-      if (p.anti[m] < 0 || p.anti[m] >= m) reps.push_back(m);
-    void *d_vc = nullptr, *d_gj = nullptr, *d_sg = nullptr, *d_reps = nullptr, *d_anti = nullptr;
-    if ((rc = dalloc(p, (void**)&p.d_Fv, size_t(P) * NR * p.M * N3 * sizeof(double2)))) return rc;
-    total += size_t(P) * NR * p.M * N3 * sizeof(double2);
+      if (!(p.fslot[m] & 1)) reps.push_back(m);
+    void *d_vc = nullptr, *d_gj = nullptr, *d_sg = nullptr, *d_reps = nullptr;
+    if ((rc = dalloc(p, (void**)&p.d_Fv, size_t(P) * NR * p.n_fslot * N3 * sizeof(double2)))) return rc;
+    total += size_t(P) * NR * p.n_fslot * N3 * sizeof(double2);
     if ((rc = up_tmp(vcoef.data(), vcoef.size(), &d_vc))) return rc;
     if ((rc = up_tmp(gj.data(), gj.size(), &d_gj))) return rc;
     if ((rc = up_tmp(p.sigma.data(), p.sigma.size(), &d_sg))) return rc;
     if ((rc = up_tmp(reps.data(), reps.size(), &d_reps))) return rc;
-    if ((rc = up_tmp(p.anti.data(), p.anti.size(), &d_anti))) return rc;
     if ((rc = launch_vss_tables(p, static_cast<double*>(d_vc), static_cast<double*>(d_gj), n_t,
-                                static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()),
-                                static_cast<int*>(d_anti))))
+                                static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()))))
       return rc;
     if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale), NL))) return rc;
     if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
@@ -595,24 +613,15 @@ int upload_plan(Plan& p) {
   if (p.precision == DGFS_FP32) {
     // the FP32 kernel reads FP32 gain tables: each FP64 value rounded once here instead of
     // converted per element in the kernel (GB300's FP64 rate is a small fraction of its FP32
-    // rate); a halved self pair's representative slot takes F(sigma) + F(-sigma), the sum the
-    // FP64 kernel forms, so the FP32 results are unchanged bit for bit
-    const size_t nF = size_t(P) * NR * (p.vss ? size_t(p.M) : 1) * N3;
-    void* d_pair_sum = nullptr;
+    // rate); with an antipodal design a self pair's slots take F(sigma) + F(-sigma) =
+    // 2 Re F(sigma), the sum the FP64 kernel forms, so the FP32 results are unchanged bit for bit
+    const size_t nF = size_t(P) * NR * (p.vss ? size_t(p.n_fslot) : 1) * N3;
     if (p.vss) {
-      std::vector<int> pair_sum(p.M, -1);
-      for (const TaskDesc& tk : p.tasks)
-        if (tk.i == tk.j && tk.out1 < 0)
-          for (int e = 0; e < tk.n_ent; ++e) {
-            const int m0 = p.ent_m[2 * (tk.ent_off + e)], m1 = p.ent_m[2 * (tk.ent_off + e) + 1];
-            if (m1 >= 0) pair_sum[m0] = m1;
-          }
-      if ((rc = up_tmp(pair_sum.data(), pair_sum.size(), &d_pair_sum))) return rc;
       if ((rc = dalloc(p, (void**)&p.d_Fvf, nF * sizeof(float2)))) return rc;
     } else {
       if ((rc = dalloc(p, (void**)&p.d_Fwf, nF * sizeof(float)))) return rc;
     }
-    if ((rc = launch_gain_tables_f32(p, static_cast<const int*>(d_pair_sum)))) return rc;
+    if ((rc = launch_gain_tables_f32(p, p.antipodal ? 1 : 0))) return rc;
     const size_t nG = size_t(P) * N3;
     if ((rc = dalloc(p, (void**)&p.d_Gmf, nG * sizeof(float)))) return rc;
     if ((rc = launch_to_f32(p, p.d_Gm, p.d_Gmf, nG))) return rc;

@@ -1,10 +1,11 @@
 // On-device construction of the FP64 weight tables of a plan (the plan's own stream):
 //   VHS  Fw[o][q][k]    = w_q 4 pi b_o rho_q^(4 - 2 omega_o) / N^3 * sinc(pi rho_q c_j |k| / L)
-//   VSS  Fv[o][q][m][k] = w_q 2 pi b_o rho_q^(4 - 2 omega_o) / N^3
+//   VSS  Fv[o][q][r][k] = w_q 2 pi b_o rho_q^(4 - 2 omega_o) / N^3
 //                         * sum_t w_t exp(-i a t cos th) J0(a sqrt(1 - t^2) sin th),
-//        a = pi rho_q c_j |k| / L, cos th = k_hat . sigma_m, (t, w_t) the Gauss-Jacobi rule of
-//        the weight (1 + t)^(alpha_o - 1)  (the sphere integral of Eq. GG with the azimuth
-//        integrated to J0); F(k, -sigma) = conj F(k, sigma) gives the antipodes
+//        a = pi rho_q c_j |k| / L, cos th = k_hat . sigma_m, m = reps[r], (t, w_t) the
+//        Gauss-Jacobi rule of the weight (1 + t)^(alpha_o - 1)  (the sphere integral of
+//        Eq. GG with the azimuth integrated to J0); one slot r per antipodal pair of
+//        directions, since F(k, -sigma) = conj F(k, sigma)
 //   loss Gm[o][k]       = sum_q (8 pi^2 2^alpha / alpha) b_o w_q rho_q^(4 - 2 omega_o) sinc(pi rho_q |k| / L)
 // (the radial weight and the 1/N^3 of the forward transform folded into F).  The per-(pair,
 // rho) prefactors and scales and the quadrature nodes come from the host; the N^3-sized
@@ -43,9 +44,9 @@ __global__ void loss_table_kernel(double* __restrict__ Gm, size_t count, int N, 
   }
 }
 
-__global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int M, int N, const double* __restrict__ coef,
+__global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int N, const double* __restrict__ coef,
                                  const double* __restrict__ gj, int n_t, const double* __restrict__ sigma,
-                                 const int* __restrict__ reps, int n_reps, const int* __restrict__ anti) {
+                                 const int* __restrict__ reps, int n_reps) {
   const size_t N3 = size_t(N) * N * N;
   const size_t count = size_t(P) * NR * n_reps * N3;
   for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < count; idx += size_t(gridDim.x) * blockDim.x) {
@@ -71,9 +72,7 @@ __global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int M,
       im -= sv * j;
     }
     const double pref = coef[2 * oq];
-    Fv[(oq * M + m) * N3 + n] = make_double2(pref * re, pref * im);
-    const int am = anti[m];
-    if (am >= 0 && am != m) Fv[(oq * M + am) * N3 + n] = make_double2(pref * re, -pref * im);
+    Fv[(oq * n_reps + r) * N3 + n] = make_double2(pref * re, pref * im);
   }
 }
 
@@ -82,21 +81,14 @@ __global__ void gain_to_f32_kernel(const double* __restrict__ src, float* __rest
     dst[i] = float(src[i]);
 }
 
-__global__ void vss_to_f32_kernel(const double2* __restrict__ src, float2* __restrict__ dst, int s, int NR, int M,
-                                  size_t N3, const int* __restrict__ pair_sum) {
-  const size_t n = size_t(s) * s * NR * M * N3;
+__global__ void vss_to_f32_kernel(const double2* __restrict__ src, float2* __restrict__ dst, int s, int NR,
+                                  int n_slot, size_t N3, int self_sum) {
+  const size_t n = size_t(s) * s * NR * n_slot * N3;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const size_t k = i % N3;
-    const int m = int((i / N3) % M);
-    const size_t oq = i / (N3 * M);
-    const int o = int(oq / NR);
+    const int o = int(i / (N3 * n_slot * NR));
     double2 v = src[i];
-    const int am = pair_sum ? pair_sum[m] : -1;
-    if (o / s == o % s && am >= 0) {
-      const double2 w = src[(oq * M + am) * N3 + k];
-      v.x += w.x;
-      v.y += w.y;
-    }
+    // F(sigma) + F(-sigma) = F + conj F
+    if (self_sum && o / s == o % s) v = make_double2(v.x + v.x, 0.0);
     dst[i] = make_float2(float(v.x), float(v.y));
   }
 }
@@ -108,16 +100,16 @@ int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n) {
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 
-int launch_gain_tables_f32(Plan& p, const int* d_pair_sum) {
+int launch_gain_tables_f32(Plan& p, int self_sum) {
   const size_t N3 = size_t(p.N) * p.N * p.N;
   const size_t P = size_t(p.s) * p.s;
   if (!p.vss) {
     const size_t n = P * p.N_rho * N3;
     gain_to_f32_kernel<<<unsigned(n / 256 + 1 < 8192 ? n / 256 + 1 : 8192), 256, 0, p.home>>>(p.d_Fw, p.d_Fwf, n);
   } else {
-    const size_t n = P * p.N_rho * p.M * N3;
+    const size_t n = P * p.N_rho * p.n_fslot * N3;
     vss_to_f32_kernel<<<unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536), 256, 0, p.home>>>(
-        p.d_Fv, p.d_Fvf, p.s, p.N_rho, p.M, N3, d_pair_sum);
+        p.d_Fv, p.d_Fvf, p.s, p.N_rho, p.n_fslot, N3, self_sum);
   }
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
@@ -131,12 +123,12 @@ int launch_loss_table(Plan& p, const double* d_gcoef, const double* d_gscale, in
 }
 
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
-                      const int* d_reps, int n_reps, const int* d_anti) {
+                      const int* d_reps, int n_reps) {
   const size_t N3 = size_t(p.N) * p.N * p.N;
   const size_t n = size_t(p.s) * p.s * p.N_rho * n_reps * N3;
   const unsigned blocks = unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536);
-  vss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Fv, p.s * p.s, p.N_rho, p.M, p.N, d_fcoef, d_gj, n_t, d_sigma,
-                                               d_reps, n_reps, d_anti);
+  vss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Fv, p.s * p.s, p.N_rho, p.N, d_fcoef, d_gj, n_t, d_sigma,
+                                               d_reps, n_reps);
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 

@@ -51,11 +51,46 @@ def test_vss_mixed_alpha_per_pair():
     assert check(gpu_collision(f, precision="fp64", **kw), oracle_collision(f, **kw), "fp64")
 
 
-def test_vss_non_antipodal_rule():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vss_non_antipodal_rule(precision):
+    """A rule without antipodes: one table slot per direction, no conjugate reads."""
     rng = np.random.default_rng(12)
     sigma = rng.normal(size=(5, 3))
     sigma /= np.linalg.norm(sigma, axis=1, keepdims=True)
     kw = dict(N=8, L=4.0, masses=(1.0, 2.0), omega=0.74, alpha=1.4, N_rho=2, sigma=sigma,
               w_sigma=np.full(5, 4 * np.pi / 5))
     f = _inputs(8, 4.0, (1.0, 2.0), 2, seed=93)
-    assert check(gpu_collision(f, precision="fp64", **kw), oracle_collision(f, **kw), "fp64")
+    assert check(gpu_collision(f, precision=precision, **kw), oracle_collision(f, **kw), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vss_negated_design(precision):
+    """The icosahedron with every direction negated: the stored direction of each antipodal
+    pair (the lower index) is now the one a halved self pair does not use, so the self pairs
+    and the reused (j,i) outputs take the other side of the conjugate symmetry
+    F(k, rho, -sigma) = conj F(k, rho, sigma)."""
+    sigma, w = quadrature.spherical_design(12)
+    kw = dict(N=8, L=4.0, masses=(1.0, 1.7, 3.0), omega=0.74, alpha=1.4, N_rho=2, sigma=-sigma,
+              w_sigma=w)
+    f = _inputs(8, 4.0, (1.0, 1.7, 3.0), 2, seed=95)
+    assert check(gpu_collision(f, precision=precision, **kw), oracle_collision(f, **kw), precision)
+
+
+@pytest.mark.parametrize("antipodal", [True, False])
+def test_vss_table_holds_one_slot_per_antipodal_pair(antipodal):
+    """F(k, rho, -sigma) = conj F(k, rho, sigma): the FP32 gain table holds one complex slot
+    per (pair, rho) and antipodal pair of directions, and one per direction without an
+    antipode: M/2 for the icosahedron, M/2 + 1 once one direction is moved off its antipode."""
+    N, s, M, NR = 8, 2, 12, 3
+    sigma, w = quadrature.spherical_design(M)
+    if not antipodal:
+        sigma = sigma.copy()
+        sigma[0] = np.array([0.6, 0.0, 0.8])   # breaks the antipode of one direction
+    plan = dgfs.Plan(N, 4.0, [1.0, 2.0], 0.74, alpha=1.4, M=M, N_rho=NR, precision="fp32",
+                     sigma=sigma, w_sigma=w)
+    tables, _ = plan.bytes(0)
+    plan.close()
+    slots = M // 2 if antipodal else M // 2 + 1
+    gain = s * s * NR * slots * N ** 3 * 8
+    loss = s * s * N ** 3 * 4
+    assert gain + loss <= tables < gain + loss + (1 << 20)

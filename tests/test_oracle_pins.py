@@ -102,6 +102,23 @@ def test_gain_weight_against_brute_force_sphere(alpha):
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def test_vss_gain_weight_at_antipode_is_conjugate():
+    """F(k, rho, -sigma) = conj F(k, rho, sigma): flipping sigma flips the sign of the plane
+    wave's phase in the sphere integral of Eq. GG once g_hat -> -g_hat is substituted, B
+    depending only on sigma.g_hat.  The brute-force sphere rule at -sigma is compared with the
+    conjugate of the J0 form at sigma (the symmetry that lets a table keep one direction of
+    each antipodal pair)."""
+    rng = np.random.default_rng(4)
+    k = rng.integers(-6, 6, size=(20, 3)).astype(float)
+    sigma = rng.normal(size=3)
+    sigma /= np.linalg.norm(sigma)
+    rho, cj, b, omega, alpha, L = 1.9, 0.61, 0.13, 0.74, 1.4, 5.0
+    at = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], rho, sigma, cj, b, omega, alpha, L)
+    anti = direct.gain_weight_by_quadrature(k, rho, -sigma, cj, b, omega, alpha, L, 60, 96)
+    assert np.max(np.abs(np.imag(at))) > 1e-3 * np.max(np.abs(at))   # not trivially real
+    assert np.max(np.abs(anti - np.conj(at))) < 1e-12 * np.max(np.abs(at))
+
+
 def test_vss_gain_weight_reduces_to_vhs():
     k = np.array([[0., 0., 0.], [1., 2., 3.], [-4., 1., 0.]])
     sigma = np.array([0.0, 0.6, 0.8])

@@ -104,7 +104,6 @@ struct Plan {
   int n_fslot = 0;              // slots per (pair, rho) of the VSS table
   bool antipodal = false;       // every direction has an antipode of equal weight
   std::vector<int> ent_ysh;     // [entries] shares the previous entry's y pass
-  std::vector<int> anti;        // antipode of every design direction, -1 if none
   int max_ent = 0;
   bool vss = false;             // some alpha_ij != 1
 

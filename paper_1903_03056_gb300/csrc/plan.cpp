@@ -339,7 +339,6 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     }
     if (anti[m] < 0) antipodal = false;
   }
-  p.anti = antipodal ? anti : std::vector<int>(M, -1);
   p.antipodal = antipodal;
   // slots of the VSS gain table: F(k, rho, -sigma) = conj F(k, rho, sigma) (the sphere
   // integral of Eq. GG with the plane wave's sign flipped), so a direction whose negation owns

@@ -103,8 +103,13 @@ typedef struct {
 /* Build the tables (Gauss-Legendre rule, design, b_ij of Eq. NVSS, R of Eq. domain, gain
  * weights F^(ij)(k, rho) of Eq. GG and loss weights G^(ij)-(k), computed in FP64, the
  * N^3-sized ones on the device; a DGFS_FP32 plan keeps them rounded once to FP32) and the
- * workspace on the current device.  *out receives the plan.  Device memory is allocated stream-ordered on a stream the plan owns; the call
- * returns when the plan is ready and never synchronises other streams. */
+ * workspace on the current device.  *out receives the plan.  Device memory is allocated
+ * stream-ordered on a stream the plan owns; the call returns when the plan is ready and
+ * never synchronises other streams.  Errors, before any device work: DGFS_ERR_UNSUPPORTED_N
+ * for N outside the list of the N field; DGFS_ERR_INVALID_ARG for a field outside its stated range,
+ * a non-finite mass, b_ij, kappa, weight or R, a direction that is not a unit vector, an
+ * unknown flag, or R > 0 with DGFS_PER_PAIR_R.  DGFS_ERR_OOM when the tables or the
+ * workspace do not fit. */
 int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out);
 
 /* Release the plan's device memory.  Waits for the plan's most recent evaluation (not for

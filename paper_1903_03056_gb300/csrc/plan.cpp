@@ -274,9 +274,12 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     }
   p.b.assign(s * s, 0.0);
   for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j)
+    for (int j = 0; j < s; ++j) {
       p.b[i * s + j] = d->b_override ? d->b_override[i * s + j]
                                      : vss_prefactor(p.mass[i], p.mass[j], p.omega[i * s + j], p.alpha[i * s + j]);
+      if (!std::isfinite(p.b[i * s + j])) return DGFS_ERR_INVALID_ARG;
+    }
+  if (!std::isfinite(d->R)) return DGFS_ERR_INVALID_ARG;
   // sphere rule
   p.M = d->M;
   if (d->sigma) {
@@ -291,6 +294,8 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   }
   if (d->w_sigma) p.w_sigma.assign(d->w_sigma, d->w_sigma + d->M);
   else p.w_sigma.assign(d->M, 4.0 * kPi / d->M);
+  for (int m = 0; m < d->M; ++m)
+    if (!std::isfinite(p.w_sigma[m])) return DGFS_ERR_INVALID_ARG;
   // radial truncation: R = 2S, S the largest support allowed by Eq. domain for every pair
   // (S_ij for the pair alone, the minimum over the pairs for the common R)
   std::vector<double> S_pair(size_t(s) * s);

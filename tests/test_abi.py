@@ -52,6 +52,10 @@ def _desc(**kw):
     (dict(flags=16), dgfs.DGFS_ERR_INVALID_ARG),
     (dict(flags=8, R=4.0), dgfs.DGFS_ERR_INVALID_ARG),   # per-pair truncation computes its own R
     (dict(kappa=[1.0, float("nan"), 1.0, 1.0], flags=2), dgfs.DGFS_ERR_INVALID_ARG),
+    (dict(b_override=[1.0, float("inf"), 1.0, 1.0]), dgfs.DGFS_ERR_INVALID_ARG),
+    (dict(R=float("inf")), dgfs.DGFS_ERR_INVALID_ARG),
+    (dict(M=6, sigma=[[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]],
+          w_sigma=[1.0, float("nan"), 1.0, 1.0, 1.0, 1.0]), dgfs.DGFS_ERR_INVALID_ARG),
 ])
 def test_invalid_plans_rejected_before_device_work(lib, kw, code):
     desc, keep = _desc(**kw)

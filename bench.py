@@ -172,25 +172,41 @@ def _oracle_node(args):
     return time.perf_counter() - t0
 
 
-def run_oracle_sample(nodes, workers):
-    """Time the FP64 oracle on `nodes` nodes with a spawn pool of `workers` processes."""
-    ctx = mp.get_context("spawn")
-    env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    try:
-        with ctx.Pool(workers) as pool:
-            pool.map(_oracle_node, [(WORKLOAD_KEY, 0)] * workers)  # import warm-up
-            t0 = time.perf_counter()
-            pool.map(_oracle_node, [(WORKLOAD_KEY, n) for n in nodes])
-            wall = time.perf_counter() - t0
-    finally:
-        for k, v in env_backup.items():
+class OraclePool:
+    """A spawn pool of single-threaded oracle workers (spawn: a pool forked after CUDA was
+    initialised can hang).  Each call times one sample of nodes, one node per task."""
+
+    def __init__(self, workers, key=None):
+        self.workers = workers
+        self.key = key or WORKLOAD_KEY
+        self.env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        self.pool = mp.get_context("spawn").Pool(workers)
+        self.pool.map(_oracle_node, [(self.key, 0)] * workers)  # import warm-up
+
+    def sample(self, nodes):
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_node, [(self.key, n) for n in nodes])
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for k, v in self.env_backup.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return wall
+
+
+def run_oracle_sample(nodes, workers):
+    """Time the FP64 oracle on `nodes` nodes with a spawn pool of `workers` processes."""
+    pool = OraclePool(workers)
+    try:
+        return pool.sample(nodes)
+    finally:
+        pool.close()
 
 
 def cpu_baseline(w, cores):
@@ -201,29 +217,40 @@ def cpu_baseline(w, cores):
                       "DFT matrices, literal (rho, sigma, pair) loop), %.1f s wall" % (len(nodes), w.batch, wall)}
 
 
-def reference_arm(args):
+def reference_arm(args, key=None):
+    """The oracle timed on the host cores: W untimed and K timed steps, each a sample of one
+    node per core taken from the bench workload's batch (consecutive node ranges).  Under
+    torchrun only rank 0 runs it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
-        return
-    w = workload()
+        return None
+    from paper_1903_03056_gb300 import synth
+    w = synth.WORKLOADS[key] if key else workload()
     cores = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        pass  # the oracle has no state to warm beyond its process pool (warmed inside)
-    times = []
-    nodes_per_step = cores
-    ctx_pool_nodes = [list(range(k * nodes_per_step, (k + 1) * nodes_per_step)) for k in range(args.steps)]
-    for nodes in ctx_pool_nodes:
-        times.append(run_oracle_sample(nodes, cores))
+    pool = OraclePool(cores, key)
+    try:
+        step = 0
+        for _ in range(args.warmup):
+            pool.sample([(step * cores + c) % w.batch for c in range(cores)])
+            step += 1
+        times = []
+        for _ in range(args.steps):
+            times.append(pool.sample([(step * cores + c) % w.batch for c in range(cores)]))
+            step += 1
+    finally:
+        pool.close()
     per_step = sum(times) / len(times)
-    value = nodes_per_step / per_step
+    value = cores / per_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d nodes per step on %d host cores" % (nodes_per_step, cores)},
+                             "sample": "%d nodes per step (one per host core) of the %d-node batch, "
+                                       "FP64 numpy oracle" % (cores, w.batch)},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return line
 
 
 # ---- GPU arm ---------------------------------------------------------------------------------

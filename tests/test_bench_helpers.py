@@ -46,3 +46,29 @@ def test_bench_workload_flops():
     n3 = 32 ** 3
     assert bench.flops_per_transform(32) == 5 * n3 * math.log2(n3)
     assert abs(bench.transforms_per_node(w) * bench.flops_per_transform(32) - 2.0299776e9) < 1.0
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    """`bench.py --impl reference`: the oracle on the host cores, W untimed and K timed steps,
+    one JSON line with the reference keys (on the small single-node workload here)."""
+    import argparse
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    args = argparse.Namespace(gpus=1, steps=2, warmup=1)
+    line = bench.reference_arm(args, key="single_node_n16")
+    printed = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert printed == line
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "evals/s" and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["dtype"] == "f64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    assert line["e2e"] == {"value": line["value"], "unit": "evals/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
+    import argparse
+    monkeypatch.setenv("RANK", "1")
+    assert bench.reference_arm(argparse.Namespace(gpus=2, steps=1, warmup=0)) is None
+    assert capsys.readouterr().out == ""

@@ -161,6 +161,14 @@ int dgfs_ssp_rk2_step(dgfs_plan plan, void* f_dev, double dt, int batch, void* s
  * different streams then share the SMs instead of queueing behind one another (serving). */
 int dgfs_plan_set_sm_share(dgfs_plan plan, double share);
 
+/* Workspace integrity check (a stand-in for a memory checker): the plan's workspace lies
+ * between two 4 KB guard blocks of a fixed byte pattern written at plan creation.  After the
+ * plan's most recent evaluation (waited for on the plan's own stream; evaluations recorded
+ * into a CUDA graph must have completed before the call), both blocks are read back and
+ * *intact = 1 when every byte still holds the pattern, 0 when a kernel wrote outside the
+ * workspace.  Errors: DGFS_ERR_INVALID_ARG (null plan or pointer), DGFS_ERR_CUDA. */
+int dgfs_plan_check(dgfs_plan plan, int* intact);
+
 /* Kernels enqueued by the most recent evaluation on this plan. */
 int dgfs_plan_launches(dgfs_plan plan, int* launches);
 

@@ -71,7 +71,7 @@ def build(force=False, verbose=False):
         fh.write("\n".join(log))
     objs = [obj for _, obj, _ in results]
     tmp = LIB + ".tmp"
-    res = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    res = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"], capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
         raise RuntimeError("link failed")

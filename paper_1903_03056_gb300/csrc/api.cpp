@@ -26,6 +26,7 @@ bool aligned16(const void* p) { return (reinterpret_cast<std::uintptr_t>(p) & 15
 // collision kernel, then (flags) the conservation projection and the species sum;
 // returns the number of kernels enqueued through *launches
 int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+  dgfs::NvtxRange range("dgfs collision");
   p.last_launches = 0;
   // the plan's workspace and work counter serve one kernel at a time: an evaluation enqueued
   // on another stream than the previous one waits for it.  Launches recorded into a CUDA graph
@@ -48,10 +49,12 @@ int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
   if (rc != DGFS_OK) return rc;
   p.last_launches = 1;
   if (p.flags & DGFS_CONSERVE) {
+    dgfs::NvtxRange r2("dgfs conservation projection");
     if ((rc = dgfs::launch_conserve(p, Qfull, batch, st)) != DGFS_OK) return rc;
     p.last_launches += 1;
   }
   if (sum) {
+    dgfs::NvtxRange r2("dgfs species sum");
     if ((rc = dgfs::launch_species_sum(p, Qfull, Q, batch, st)) != DGFS_OK) return rc;
     p.last_launches += 1;
   }
@@ -73,6 +76,7 @@ extern "C" {
 
 int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out) {
   if (!desc || !out) return DGFS_ERR_INVALID_ARG;
+  dgfs::NvtxRange range("dgfs_create_plan");
   *out = nullptr;
   dgfs_plan_s* h = new (std::nothrow) dgfs_plan_s;
   if (!h) return DGFS_ERR_OOM;
@@ -118,6 +122,7 @@ int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, i
   if (!f_host || !Q_host) return DGFS_ERR_INVALID_ARG;
   dgfs::Plan& p = plan->plan;
   if (batch > p.max_batch) return DGFS_ERR_BUDGET;
+  dgfs::NvtxRange range("dgfs_eval_collision_host");
   DeviceGuard g(p.device);
   if (!g.ok) return DGFS_ERR_CUDA;
   const size_t n3 = size_t(p.N) * p.N * p.N;
@@ -189,6 +194,7 @@ int dgfs_ssp_rk2_step(dgfs_plan plan, void* f_dev, double dt, int batch, void* s
   if (batch == 0) return DGFS_OK;
   if (!f_dev || !aligned16(f_dev)) return DGFS_ERR_INVALID_ARG;
   if (batch > p.max_batch) return DGFS_ERR_BUDGET;
+  dgfs::NvtxRange range("dgfs_ssp_rk2_step");
   DeviceGuard g(p.device);
   if (!g.ok) return DGFS_ERR_CUDA;
   const size_t n = size_t(p.max_batch) * p.s * p.N * p.N * p.N;
@@ -227,7 +233,7 @@ int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace
   const size_t n3 = size_t(p.N) * p.N * p.N;
   if (tables) *tables = p.table_bytes;
   if (workspace)
-    *workspace = p.scratch_bytes + (p.d_Qfull ? size_t(p.max_batch) * p.s * p.s * n3 * dgfs::real_size(p) : 0) +
+    *workspace = p.scratch_bytes + 2 * dgfs::Plan::kGuardBytes + (p.d_Qfull ? size_t(p.max_batch) * p.s * p.s * n3 * dgfs::real_size(p) : 0) +
                  size_t(batch) * (p.s + output_pairs(p)) * n3 * dgfs::real_size(p);
   return DGFS_OK;
 }
@@ -235,6 +241,30 @@ int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace
 int dgfs_plan_radius(dgfs_plan plan, double* R) {
   if (!plan || !R) return DGFS_ERR_INVALID_ARG;
   *R = plan->plan.R;
+  return DGFS_OK;
+}
+
+int dgfs_plan_check(dgfs_plan plan, int* intact) {
+  if (!plan || !intact) return DGFS_ERR_INVALID_ARG;
+  dgfs::Plan& p = plan->plan;
+  if (!p.d_scratch_raw) return DGFS_ERR_INVALID_ARG;
+  dgfs::NvtxRange range("dgfs_plan_check");
+  DeviceGuard g(p.device);
+  if (!g.ok) return DGFS_ERR_CUDA;
+  constexpr size_t G = dgfs::Plan::kGuardBytes;
+  static thread_local unsigned char host[2 * G];
+  // after the plan's last evaluation, on the plan's own stream
+  if ((p.has_eval && cudaStreamWaitEvent(p.home, p.last_eval, 0) != cudaSuccess) ||
+      cudaMemcpyAsync(host, p.d_scratch_raw, G, cudaMemcpyDeviceToHost, p.home) != cudaSuccess ||
+      cudaMemcpyAsync(host + G, static_cast<const char*>(p.d_scratch) + p.scratch_bytes, G, cudaMemcpyDeviceToHost,
+                      p.home) != cudaSuccess ||
+      cudaStreamSynchronize(p.home) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  int ok = 1;
+  for (size_t k = 0; k < 2 * G; ++k) ok &= host[k] == dgfs::Plan::kGuardByte ? 1 : 0;
+  *intact = ok;
   return DGFS_OK;
 }
 

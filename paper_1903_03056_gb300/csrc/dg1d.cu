@@ -472,6 +472,7 @@ int dgfs_dg_nodes(dgfs_dg_plan plan, double* x_out) {
 int dgfs_dg_transport(dgfs_dg_plan plan, const void* f_dev, void* rhs_dev, void* stream) {
   if (!plan || !f_dev || !rhs_dev || !aligned16(f_dev) || !aligned16(rhs_dev) || f_dev == rhs_dev)
     return DGFS_ERR_INVALID_ARG;
+  dgfs::NvtxRange range("dgfs_dg_transport");
   DevGuard g(plan->coll->plan.device);
   if (!g.ok) return DGFS_ERR_CUDA;
   return transport(*plan, 0, f_dev, nullptr, nullptr, rhs_dev, 0.0, static_cast<cudaStream_t>(stream));
@@ -482,6 +483,7 @@ int dgfs_dg_step(dgfs_dg_plan plan, void* f_dev, double dt, void* stream) {
   const dgfs::Plan& p = plan->coll->plan;
   if (!(p.flags & DGFS_SUM_SPECIES)) return DGFS_ERR_INVALID_ARG;
   if (plan->B > p.max_batch) return DGFS_ERR_BUDGET;
+  dgfs::NvtxRange range("dgfs_dg_step");
   DevGuard g(p.device);
   if (!g.ok) return DGFS_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "dgfs.h"
 
@@ -130,7 +131,10 @@ struct Plan {
 
   // workspace
   LaunchShape shape;
-  void* d_scratch = nullptr;
+  void* d_scratch = nullptr;       // kGuardBytes into d_scratch_raw
+  void* d_scratch_raw = nullptr;   // guard | workspace | guard
+  static constexpr size_t kGuardBytes = 4096;
+  static constexpr unsigned char kGuardByte = 0xA5;
   unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel
   size_t scratch_bytes = 0;
   void* d_rk = nullptr;             // SSP-RK2 workspace: f1 and the right-hand side
@@ -145,6 +149,16 @@ struct Plan {
 };
 
 size_t real_size(const Plan& p);
+
+// NVTX range over a scope of host code (plan construction, evaluation stages): shown by
+// profilers on the CPU timeline and usable as a kernel filter (ncu --nvtx); a no-op without
+// an attached tool
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // host plan construction (plan.cpp)
 int build_plan(const dgfs_plan_desc* d, Plan& p);

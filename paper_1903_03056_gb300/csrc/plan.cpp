@@ -657,7 +657,16 @@ int upload_plan(Plan& p) {
   if ((p.flags & DGFS_SUM_SPECIES) && p.max_batch > 0) {
     if ((rc = dalloc(p, &p.d_Qfull, size_t(p.max_batch) * s * s * N3 * real_size(p)))) return rc;
   }
-  if ((rc = dalloc(p, &p.d_scratch, p.scratch_bytes))) return rc;
+  // the workspace between two guard blocks of a fixed byte pattern: dgfs_plan_check reads
+  // them back to detect a kernel write outside the workspace
+  if ((rc = dalloc(p, &p.d_scratch_raw, p.scratch_bytes + 2 * Plan::kGuardBytes))) return rc;
+  p.d_scratch = static_cast<char*>(p.d_scratch_raw) + Plan::kGuardBytes;
+  if (cudaMemsetAsync(p.d_scratch_raw, Plan::kGuardByte, Plan::kGuardBytes, p.home) != cudaSuccess ||
+      cudaMemsetAsync(static_cast<char*>(p.d_scratch) + p.scratch_bytes, Plan::kGuardByte, Plan::kGuardBytes,
+                      p.home) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
   if ((rc = dalloc(p, (void**)&p.d_counter, 256))) return rc;
   // the host arrays above must outlive the copies
   if (cudaStreamSynchronize(p.home) != cudaSuccess) return DGFS_ERR_CUDA;
@@ -666,7 +675,7 @@ int upload_plan(Plan& p) {
 
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
-                  p.d_scratch, p.d_stage_f, p.d_stage_Q, p.d_cons,  p.d_kappa, p.d_Qfull, p.d_ent_m,
+                  p.d_scratch_raw, p.d_stage_f, p.d_stage_Q, p.d_cons, p.d_kappa, p.d_Qfull, p.d_ent_m,
                   p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf};
   if (p.home) {
     for (void* q : ptrs)
@@ -690,7 +699,7 @@ void free_plan(Plan& p) {
   p.ev_start = nullptr;
   p.h2d = p.d2h = nullptr;
   p.d_Fw = p.d_Gm = p.d_ent_w = nullptr;
-  p.d_phase = p.d_scratch = p.d_stage_f = p.d_stage_Q = nullptr;
+  p.d_phase = p.d_scratch = p.d_scratch_raw = p.d_stage_f = p.d_stage_Q = nullptr;
   p.d_tasks = nullptr;
   p.d_groups = nullptr;
   p.d_cons = nullptr;

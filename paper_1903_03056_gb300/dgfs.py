@@ -37,7 +37,7 @@ DGFS_SIDE_INFLOW = 1
 
 EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
-           "dgfs_plan_launches", "dgfs_strerror", "dgfs_eval_collision_noalloc",
+           "dgfs_plan_launches", "dgfs_plan_check", "dgfs_strerror", "dgfs_eval_collision_noalloc",
            "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step", "dgfs_dg_create", "dgfs_dg_destroy",
            "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step")
 
@@ -84,6 +84,7 @@ def load():
     lib.dgfs_plan_bytes.argtypes = [vp, ci, ctypes.POINTER(cs), ctypes.POINTER(cs)]
     lib.dgfs_plan_radius.argtypes = [vp, _dptr]
     lib.dgfs_plan_launches.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.dgfs_plan_check.argtypes = [vp, ctypes.POINTER(ci)]
     lib.dgfs_eval_collision_noalloc.argtypes = [ctypes.POINTER(dgfs_plan_desc), vp, vp, ci, vp]
     lib.dgfs_plan_set_sm_share.argtypes = [vp, ctypes.c_double]
     lib.dgfs_ssp_rk2_step.argtypes = [vp, vp, ctypes.c_double, ci, vp]
@@ -142,6 +143,12 @@ def dgfs_plan_launches(plan):
     n = ctypes.c_int()
     code = load().dgfs_plan_launches(plan, ctypes.byref(n))
     return code, n.value
+
+
+def dgfs_plan_check(plan):
+    ok = ctypes.c_int()
+    code = load().dgfs_plan_check(plan, ctypes.byref(ok))
+    return code, bool(ok.value)
 
 
 def dgfs_strerror(code):
@@ -270,6 +277,13 @@ class Plan:
         """One SSP-RK2 step of d_t f_i = sum_j kappa_ij Q_ij, in place on the CUDA tensor f."""
         _check(dgfs_ssp_rk2_step(self.handle, f.data_ptr(), float(dt), int(f.shape[0]),
                                  _stream_handle(stream)), "dgfs_ssp_rk2_step")
+
+    def check(self):
+        """True when the guard blocks around the plan's workspace are intact after its most
+        recent evaluation (no kernel wrote outside the workspace)."""
+        code, ok = dgfs_plan_check(self.handle)
+        _check(code, "dgfs_plan_check")
+        return ok
 
     def set_sm_share(self, share):
         _check(dgfs_plan_set_sm_share(self.handle, float(share)), "dgfs_plan_set_sm_share")

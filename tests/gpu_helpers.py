@@ -20,9 +20,22 @@ def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", si
     plan = dgfs.Plan(N, L, masses, omega, alpha=alpha, M=M, N_rho=N_rho, precision=precision,
                      sigma=sigma, w_sigma=w_sigma, b_override=b_override, R=R, flags=flags)
     fd = torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=dt)
-    Q = plan.eval(fd)
+    f_before = fd.clone()
+    # Q between two margins of a sentinel value: nothing outside Q may be written, every
+    # element of Q must be
+    B, s = f.shape[0], len(masses)
+    n_out = B * s * s * N ** 3
+    pad = 4096
+    buf = torch.full((n_out + 2 * pad,), 1.25e30, dtype=dt, device="cuda")
+    Q = buf[pad:pad + n_out].view(B, s, s, N, N, N)
+    plan.eval(fd, Q)
     torch.cuda.synchronize()
     assert plan.launches() == 1
+    assert plan.check(), "a kernel wrote outside the plan's workspace"
+    assert bool((buf[:pad] == 1.25e30).all()) and bool((buf[pad + n_out:] == 1.25e30).all()), \
+        "a kernel wrote outside Q"
+    assert not bool((Q == 1.25e30).any()), "an element of Q was not written"
+    assert torch.equal(fd, f_before), "the input was modified"
     out = Q.double().cpu().numpy()
     plan.close()
     return out

@@ -70,6 +70,7 @@ def test_null_arguments(lib):
     assert dgfs.dgfs_eval_collision_host(None, None, None, 1, None) == dgfs.DGFS_ERR_INVALID_ARG
     assert dgfs.dgfs_destroy_plan(None) == dgfs.DGFS_ERR_INVALID_ARG
     assert dgfs.dgfs_plan_radius(None)[0] == dgfs.DGFS_ERR_INVALID_ARG
+    assert dgfs.dgfs_plan_check(None)[0] == dgfs.DGFS_ERR_INVALID_ARG
 
 
 def test_strerror_names_every_code(lib):

@@ -51,6 +51,7 @@ def _eval(w, f, precision, nodes=None):
     fd = torch.from_numpy(np.ascontiguousarray(src)).to(device="cuda", dtype=dt)
     Q = plan.eval(fd)
     torch.cuda.synchronize()
+    assert plan.check(), "a kernel wrote outside the plan's workspace"
     plan.close()
     return Q
 

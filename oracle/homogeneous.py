@@ -5,8 +5,6 @@ Runge-Kutta scheme the paper integrates in time with:
     f1 = f + dt R(f),   f_new = f / 2 + (f1 + dt R(f1)) / 2.
 """
 
-import numpy as np
-
 from . import fast_spectral, moments
 
 

@@ -9,8 +9,6 @@ Prints one JSON line with the mean time per evaluation measured with CUDA events
 import argparse
 import json
 
-import numpy as np
-
 
 def main():
     ap = argparse.ArgumentParser()

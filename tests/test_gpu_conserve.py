@@ -4,7 +4,7 @@ DGFS_SUM_SPECIES (sum_j kappa_ij Q_ij) against the oracle's projection and sum."
 import numpy as np
 import pytest
 
-from gpu_helpers import check, max_rel_error, oracle_collision, TOL_FP32, TOL_FP64
+from gpu_helpers import check, oracle_collision, TOL_FP32, TOL_FP64
 from oracle import fast_spectral as fs, moments
 from paper_1903_03056_gb300 import build, dgfs, synth
 

@@ -4,7 +4,6 @@ their step times with one all_reduce(MAX); the whole-job rate is world * batch /
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as tmp
 

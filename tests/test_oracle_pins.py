@@ -102,6 +102,31 @@ def test_gain_weight_against_brute_force_sphere(alpha):
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def test_vss_gain_weight_closed_form_at_alpha_2():
+    """alpha = 2 makes the angular factor 1 + sigma.g_hat linear, and the sphere integral of
+    Eq. GG closes: the constant part gives 4 pi j0(a); the linear part gives
+    sigma . int g_hat exp(-i a k_hat.g_hat) dg_hat = -4 pi i j1(a) cos(theta), so
+        F = 4 pi b rho^(4 - 2 omega) (j0(a) - i cos(theta) j1(a)),
+    a = pi rho c_j |k| / L, cos(theta) = k_hat.sigma, j0 and j1 the spherical Bessel
+    functions written out from sin and cos."""
+    rng = np.random.default_rng(6)
+    k = rng.integers(-8, 8, size=(40, 3)).astype(float)
+    k[0] = 0.0
+    sigma = rng.normal(size=3)
+    sigma /= np.linalg.norm(sigma)
+    rho, cj, b, omega, L = 2.7, 0.72, 0.09, 0.66, 5.0
+    got = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], rho, sigma, cj, b, omega, 2.0, L)
+    kn = np.linalg.norm(k, axis=1)
+    a = np.pi * rho * cj * kn / L
+    with np.errstate(invalid="ignore", divide="ignore"):
+        j0 = np.where(a > 0, np.sin(a) / a, 1.0)
+        j1 = np.where(a > 0, np.sin(a) / a ** 2 - np.cos(a) / a, 0.0)
+        cos_t = np.where(kn > 0, (k @ sigma) / kn, 0.0)
+    ref = 4 * np.pi * b * rho ** (4 - 2 * omega) * (j0 - 1j * cos_t * j1)
+    assert np.max(np.abs(np.imag(ref))) > 0.1 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
 def test_vss_gain_weight_at_antipode_is_conjugate():
     """F(k, rho, -sigma) = conj F(k, rho, sigma): flipping sigma flips the sign of the plane
     wave's phase in the sphere integral of Eq. GG once g_hat -> -g_hat is substituted, B

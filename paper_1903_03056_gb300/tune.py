@@ -42,13 +42,31 @@ CANDIDATES = {
 }
 
 
+def geometry(N, C, GP, MB, csize):
+    """The kernel's compile-time geometry of a shape (the same rules as its Geo template):
+    P in registers, CTAs per SM, y-pass sharing, plane buffers per group and the shared
+    memory of the plane buffers.  csize = bytes of one complex element."""
+    preg = (csize == 8 and N <= 48) or N <= 16
+    buf = N * (N + 1) * csize
+    threads = GP * N
+    if MB > 1:
+        res = MB
+    else:
+        res = 2 if threads <= 128 and 2 * (GP * 2 * buf + 1024) <= 228 * 1024 else 1
+    ysh = N <= 16 and preg and res * (GP * 3 * buf + 1024 + 8 * 1024) <= 228 * 1024
+    nbuf = 2 if preg and not ysh else 3
+    return {"preg": preg, "res": res, "ysh": ysh, "nbuf": nbuf, "threads": threads,
+            "smem": GP * nbuf * buf}
+
+
 def valid(N, C, GP, MB, csize):
-    """Shape constraints of the kernel; csize = bytes of one complex element."""
+    """Shape constraints of the kernel: planes and pencils split evenly over the cluster and
+    the plane groups, at most 1024 threads, the plane buffers of MB CTAs in one SM's shared
+    memory, and at least 64 registers a thread at MB CTAs per SM."""
     if N % C or (N * N) % C or (N // C) % GP or GP * N > 1024:
         return False
-    nbuf = 2 if (csize == 8 and N <= 32) or N <= 16 else 3
-    smem = GP * nbuf * N * (N + 1) * csize
-    return MB * smem <= 227 * 1024 and 65536 // (GP * N * MB) >= 64
+    g = geometry(N, C, GP, MB, csize)
+    return MB * g["smem"] <= 227 * 1024 and 65536 // (g["threads"] * MB) >= 64
 
 
 def _ctype(precision):

@@ -51,7 +51,8 @@ extern "C" {
 #define DGFS_ERR_OOM (-3)            /* device or host allocation failed */
 #define DGFS_ERR_BUDGET (-4)         /* batch larger than the plan's max_batch */
 #define DGFS_ERR_CUDA (-5)           /* a CUDA runtime call or kernel launch failed */
-#define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up */
+#define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up (reserved: the
+                                        kernels of this build have no device-side waits) */
 #define DGFS_ERR_UNSUPPORTED (-7)    /* a valid request this build does not implement */
 
 /* arithmetic of the transforms, products and accumulations */

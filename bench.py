@@ -28,7 +28,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "collision evals/s at N=32^3 mixed-precision vs FP64 plain; p50/p99 stream latency"
 WORKLOAD_KEY = "dg_batch_n32"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -95,6 +94,26 @@ def measured_traffic(kernel):
     if not rec or rec.get("sources_sha1") != kernel_sources_sha1():
         return None
     return rec.get("bytes_per_launch")
+
+
+def measured_alu_peaks(torch, dgfs, local):
+    """FP32 and FP64 multiply-add rates of this GPU, measured by the library's dependent-FMA
+    loop on every SM (dgfs_measure_fma_rate), with the SM clock sampled meanwhile.  Falls back
+    to the FP32 lane count x 2 flop x the maximum clock of this device's SM count when the
+    measurement fails."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    with ClockSampler(local) as clk:
+        c32, r32 = dgfs.dgfs_measure_fma_rate("fp32")
+        c64, r64 = dgfs.dgfs_measure_fma_rate("fp64")
+    clocks = clk.summary()
+    out = {"sms": sms, "clocks": clocks}
+    if c32 == 0 and c64 == 0 and r32 > 0 and r64 > 0:
+        out.update({"fp32_tflops": r32 / 1e12, "fp64_tflops": r64 / 1e12, "source": "measured"})
+    else:
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        out.update({"fp32_tflops": sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "fp64_tflops": None,
+                    "source": "derived (measurement failed: %d, %d)" % (c32, c64)})
+    return out
 
 
 def config_dict(w):
@@ -379,6 +398,7 @@ def gpu_arm(args):
 
     # CPU baseline first (spawned pool before heavy GPU work; rank 0, N=1 only)
     cpu = cpu_baseline(w, cores) if (world == 1 and not args.no_cpu_baseline) else None
+    peaks = measured_alu_peaks(torch, dgfs, local)
 
     f64 = synth.batch_distribution(w, nodes=rank_nodes(rank, B))  # [B, s, N, N, N]
     stream = torch.cuda.Stream()
@@ -444,12 +464,18 @@ def gpu_arm(args):
 
     if rank == 0:
         achieved = flops_node * B / (ms32 * 1e-3) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        peak = peaks["fp32_tflops"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic("collision_kernel<float,32>"),
                 "kernel": "collision_kernel<float,32>",
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                "peak_note": "FP32 FMA rate %s: dependent-FMA loop on all %d SMs (dgfs_measure_fma_rate) "
+                             "at a median SM clock of %s MHz" % (peaks["source"], peaks["sms"],
+                                                                  peaks["clocks"].get("sm_mhz")),
+                "fp64_peak_tflops": peaks["fp64_tflops"],
                 "flops_per_node": flops_node}
+        if fp64 is not None and peaks["fp64_tflops"]:
+            fp64["achieved_tflops"] = flops_node * B / (fp64["ms_per_step"] * 1e-3) / 1e12
+            fp64["frac_of_fp64_peak"] = fp64["achieved_tflops"] / peaks["fp64_tflops"]
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -468,7 +494,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

@@ -176,6 +176,15 @@ int dgfs_plan_launches(dgfs_plan plan, int* launches);
 /* Static text naming a return code. */
 const char* dgfs_strerror(int code);
 
+/* Measured multiply-add rate of the current device's FP32 (precision = DGFS_FP32) or FP64
+ * (DGFS_FP64) pipe, in flop/s (2 flop per FMA): the denominator of the ALU roofline that bounds
+ * the collision kernel.  No counterpart in the paper (a measurement helper).  Runs a
+ * dependent-FMA loop on every SM for about 50 ms after two sizing launches, on the legacy
+ * default stream, and returns when done (synchronous; allocates and frees a small output
+ * buffer).  The rate is that of the SM clock during the call.  Errors: DGFS_ERR_INVALID_ARG
+ * (null pointer, other precision), DGFS_ERR_OOM, DGFS_ERR_CUDA. */
+int dgfs_measure_fma_rate(int precision, double* flop_per_s);
+
 /* The evaluation of dgfs_eval_collision for callers that cannot allocate device memory
  * (no counterpart in the paper; it exists for embedding).  A solver plugin whose host
  * application owns every device allocation, or code that may not call cudaMalloc after
@@ -192,9 +201,11 @@ const char* dgfs_strerror(int code);
  * (else DGFS_ERR_UNSUPPORTED_N), s <= 3, M <= 12, N_rho <= 16, alpha == 1 (else
  * DGFS_ERR_UNSUPPORTED); these are checked before any work.  Batches of any size run on at
  * most 64 CTAs.
- * The first call on a device looks up the workspace's device address and sets the kernels'
- * shared-memory limits (cudaGetSymbolAddress, cudaFuncSetAttribute); make that first call
- * before any stream capture.  Every call on a device shares the one workspace: calls whose
+ * The first call in a CUDA context (per device, and again after cudaDeviceReset or any other
+ * change of the device's current context) looks up the workspace's device address and sets
+ * the kernels' shared-memory limits (cudaGetSymbolAddress, cudaFuncSetAttribute); make that
+ * first call before any stream capture.  desc fields must be finite (L, R, b_override,
+ * w_sigma, sigma), else DGFS_ERR_INVALID_ARG.  Every call on a device shares the one workspace: calls whose
  * kernels overlap on the GPU (different streams, no ordering between them) race and give
  * wrong results; calls ordered on one stream do not.  Results equal dgfs_eval_collision's
  * within FP32 rounding. */

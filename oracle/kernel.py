@@ -46,7 +46,37 @@ def sinc(x):
     return np.sinc(np.asarray(x) / np.pi)
 
 
-def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=64):
+def phi_integral(a, cos_t, alpha, n_t):
+    """int_{-1}^{1} (1+t)^(alpha-1) exp(-i a t cos theta) J0(a sqrt(1-t^2) sin theta) dt by the
+    n_t-point Gauss-Jacobi rule for the weight (1+t)^(alpha-1)."""
+    sin_t = np.sqrt(np.maximum(0.0, 1.0 - cos_t * cos_t))
+    t, wt = roots_jacobi(n_t, 0.0, alpha - 1.0)
+    acc = np.zeros(np.broadcast(a, cos_t).shape, dtype=np.complex128)
+    for tq, wq in zip(t, wt):
+        acc += wq * np.exp(-1j * a * tq * cos_t) * j0(a * np.sqrt(1.0 - tq * tq) * sin_t)
+    return acc
+
+
+def jacobi_rule_size(a_max, alpha, tol=1e-13):
+    """Size of the t rule that computes F "to high accuracy" (Sec. 4, the precomputation of
+    F after Eq. GG), read as a converged integral: starting from 32 points the rule is
+    doubled until, at the largest argument a_max (the integrand's highest frequency) and at
+    a spread of angles, the change is below tol times the integral's bound
+    int (1+t)^(alpha-1) dt = 2^alpha / alpha; the finer rule of the last pair is kept.
+    Lower arguments converge sooner, since the integrand's bandwidth grows with a."""
+    bound = 2.0 ** alpha / alpha
+    cos_t = np.linspace(-1.0, 1.0, 9)
+    a = np.array([a_max, 0.5 * a_max])[:, None]
+    n = 32
+    prev = phi_integral(a, cos_t, alpha, n)
+    while True:
+        cur = phi_integral(a, cos_t, alpha, 2 * n)
+        if np.max(np.abs(cur - prev)) < tol * bound or n >= 4096:
+            return 2 * n
+        n, prev = 2 * n, cur
+
+
+def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=None):
     """F^{(ij)}(k, rho, sigma) of Eq. GG:
 
         F = rho^2 * int_{S^2} B_ij(rho, sigma . g_hat) exp(-i pi rho c_j k . g_hat / L) dg_hat
@@ -62,7 +92,8 @@ def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=64):
         F = 2 pi b rho^(4-2 omega) int_{-1}^{1} (1+t)^(alpha-1) exp(-i a t cos theta)
                                              J0(a sqrt(1-t^2) sin theta) dt,
 
-    evaluated with an n_t-point Gauss-Jacobi rule for the weight (1+t)^(alpha-1).
+    evaluated with a Gauss-Jacobi rule for the weight (1+t)^(alpha-1): n_t points if given,
+    else the converged size of jacobi_rule_size at the largest a of the call.
     """
     kn = np.sqrt(kx * kx + ky * ky + kz * kz)
     a = np.pi * rho * cj * kn / L
@@ -71,12 +102,9 @@ def gain_weight(kx, ky, kz, rho, sigma, cj, b, omega, alpha, L, n_t=64):
         return (4.0 * np.pi * pref * sinc(a)).astype(np.complex128)
     with np.errstate(invalid="ignore", divide="ignore"):
         cos_t = np.where(kn > 0, (kx * sigma[0] + ky * sigma[1] + kz * sigma[2]) / kn, 1.0)
-    sin_t = np.sqrt(np.maximum(0.0, 1.0 - cos_t * cos_t))
-    t, wt = roots_jacobi(n_t, 0.0, alpha - 1.0)
-    acc = np.zeros(np.shape(a), dtype=np.complex128)
-    for tq, wq in zip(t, wt):
-        acc += wq * np.exp(-1j * a * tq * cos_t) * j0(a * np.sqrt(1.0 - tq * tq) * sin_t)
-    return 2.0 * np.pi * pref * acc
+    if n_t is None:
+        n_t = jacobi_rule_size(float(np.max(a)), alpha)
+    return 2.0 * np.pi * pref * phi_integral(a, cos_t, alpha, n_t)
 
 
 def loss_weight(kx, ky, kz, rho_nodes, rho_weights, b, omega, alpha, L):

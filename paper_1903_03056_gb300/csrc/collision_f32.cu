@@ -1,5 +1,6 @@
 // FP32 instantiations of the collision kernel: transforms, products and accumulations in
-// FP32; the gain and loss weight tables stay FP64 and are rounded on load.
+// FP32.  The gain and loss weight tables are computed in FP64 at plan creation and kept as
+// FP32 copies (each value rounded once), which is what this kernel reads.
 #include "collision_kernel.cuh"
 
 namespace dgfs {

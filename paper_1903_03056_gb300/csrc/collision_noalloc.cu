@@ -17,6 +17,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "collision_kernel.cuh"
 
 namespace dgfs {
@@ -284,18 +286,63 @@ constexpr size_t smem_bytes() {
   return size_t(N) * 2 * N * (N + 1) * sizeof(float2) + size_t(kMaxM) * 6 * N * sizeof(float2);
 }
 
-// ---- once-per-device set-up ---------------------------------------------------------------
+// ---- once-per-context set-up ----------------------------------------------------------------
+// The workspace's device address and the kernels' shared-memory limits belong to the CUDA
+// context that loaded this module.  A cudaDeviceReset, or a new primary context, reloads the
+// module, so the set-up is keyed on the current context's unique id (read through the
+// driver's cuCtxGetCurrent / cuCtxGetId, looked up by the runtime without linking the driver
+// library) and redone when that id changes.
 struct DeviceState {
+  unsigned long long ctx_id = 0;
   bool ready = false;
   float2* scratch = nullptr;
 };
 DeviceState g_state[kMaxDevices];
 std::mutex g_mutex;
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// unique id of the context current on this thread (the device's primary context when the
+// runtime made none current yet); 0 on failure
+unsigned long long current_context_id(int dev) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return 0;
+    }
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return 0;
+  if (ctx == nullptr) {
+    // no context current yet: make the device's primary context current (cudaSetDevice
+    // initialises it) and read again
+    if (cudaSetDevice(dev) != cudaSuccess || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
 int setup_device(int dev, float2** scratch) {
   if (dev < 0 || dev >= kMaxDevices) return DGFS_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_state[dev].ready) {
+  const unsigned long long ctx = current_context_id(dev);
+  if (ctx == 0) return DGFS_ERR_CUDA;
+  if (!g_state[dev].ready || g_state[dev].ctx_id != ctx) {
+    g_state[dev].ready = false;
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
       cudaGetLastError();
@@ -308,6 +355,7 @@ int setup_device(int dev, float2** scratch) {
       return DGFS_ERR_CUDA;
     }
     g_state[dev].scratch = static_cast<float2*>(ptr);
+    g_state[dev].ctx_id = ctx;
     g_state[dev].ready = true;
   }
   *scratch = g_state[dev].scratch;
@@ -315,33 +363,6 @@ int setup_device(int dev, float2** scratch) {
 }
 
 // ---- host-side constants, without heap allocation -------------------------------------------
-void gauss_legendre_fixed(int n, double R, double* rho, double* w) {
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int k = 2; k <= n; ++k) {
-        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    double p0 = 1.0, p1 = z;
-    for (int k = 2; k <= n; ++k) {
-      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
-      p0 = p1;
-      p1 = p2;
-    }
-    dp = n * (z * p1 - p0) / (z * z - 1.0);
-    rho[i] = 0.5 * R * (z + 1.0);
-    w[i] = 0.5 * R * 2.0 / ((1.0 - z * z) * dp * dp);
-  }
-}
-
 int builtin_design_fixed(int M, double (*sg)[3]) {
   const double g = (1.0 + std::sqrt(5.0)) / 2.0;
   int m = 0;
@@ -372,7 +393,8 @@ int builtin_design_fixed(int M, double (*sg)[3]) {
 int build_params(const dgfs_plan_desc* d, NoAllocParams& p) {
   if (d->precision != DGFS_FP32 || d->flags != 0u) return DGFS_ERR_UNSUPPORTED;
   if (d->N != 8 && d->N != 12 && d->N != 16) return DGFS_ERR_UNSUPPORTED_N;
-  if (!(d->L > 0.0) || d->s < 1 || !d->mass || !d->omega || !d->alpha || d->N_rho < 1 || d->M < 1)
+  if (!(d->L > 0.0) || !std::isfinite(d->L) || d->s < 1 || !d->mass || !d->omega || !d->alpha || d->N_rho < 1 ||
+      d->M < 1 || std::isnan(d->R) || std::isinf(d->R))
     return DGFS_ERR_INVALID_ARG;
   if (d->s > kMaxS || d->M > kMaxM || d->N_rho > kMaxRho) return DGFS_ERR_UNSUPPORTED;
   const int s = d->s, N = d->N, M = d->M, NR = d->N_rho;
@@ -381,18 +403,22 @@ int build_params(const dgfs_plan_desc* d, NoAllocParams& p) {
   for (int k = 0; k < s * s; ++k) {
     if (!(d->omega[k] >= 0.5 && d->omega[k] <= 1.0)) return DGFS_ERR_INVALID_ARG;
     if (d->alpha[k] != 1.0) return DGFS_ERR_UNSUPPORTED;
+    if (d->b_override && !std::isfinite(d->b_override[k])) return DGFS_ERR_INVALID_ARG;
   }
   double sg[kMaxM][3], ws[kMaxM];
   if (d->sigma) {
     for (int m = 0; m < M; ++m) {
       for (int a = 0; a < 3; ++a) sg[m][a] = d->sigma[3 * m + a];
       const double n = std::sqrt(sg[m][0] * sg[m][0] + sg[m][1] * sg[m][1] + sg[m][2] * sg[m][2]);
-      if (!(std::fabs(n - 1.0) < 1e-9)) return DGFS_ERR_INVALID_ARG;
+      if (!(std::fabs(n - 1.0) < 1e-9)) return DGFS_ERR_INVALID_ARG;  // also rejects NaN
     }
   } else if (builtin_design_fixed(M, sg) != DGFS_OK) {
     return DGFS_ERR_INVALID_ARG;
   }
-  for (int m = 0; m < M; ++m) ws[m] = d->w_sigma ? d->w_sigma[m] : 4.0 * kPi / M;
+  for (int m = 0; m < M; ++m) {
+    ws[m] = d->w_sigma ? d->w_sigma[m] : 4.0 * kPi / M;
+    if (!std::isfinite(ws[m])) return DGFS_ERR_INVALID_ARG;
+  }
   // radial truncation (Eq. domain, all pairs) and Gauss-Legendre rule
   double R = d->R;
   if (!(R > 0.0)) {
@@ -406,7 +432,11 @@ int build_params(const dgfs_plan_desc* d, NoAllocParams& p) {
     R = 2.0 * S;
   }
   double wr[kMaxRho];
-  gauss_legendre_fixed(NR, R, p.rho, wr);
+  gauss_legendre_rule(NR, p.rho, wr);
+  for (int q = 0; q < NR; ++q) {
+    p.rho[q] = 0.5 * R * (p.rho[q] + 1.0);
+    wr[q] *= 0.5 * R;
+  }
   // kernel prefactors (Eq. NVSS unless overridden) and the weight constants per pair
   const double n3 = double(N) * N * N;
   for (int i = 0; i < s; ++i)

@@ -103,6 +103,8 @@ struct Plan {
   std::vector<int> ent_m;       // [entries][2] VSS table slot codes of the entry and its antipode
   std::vector<int> fslot;       // [M] VSS table slot code of each direction: 2 slot + conj bit
   int n_fslot = 0;              // slots per (pair, rho) of the VSS table
+  int n_t = 64;                 // points of the VSS gain weight's Gauss-Jacobi rule in t
+  double vss_a_max = 0;         // largest argument pi rho c_j |k| / L of that table
   bool antipodal = false;       // every direction has an antipode of equal weight
   std::vector<int> ent_ysh;     // [entries] shares the previous entry's y pass
   int max_ent = 0;
@@ -161,6 +163,8 @@ struct NvtxRange {
 };
 
 // host plan construction (plan.cpp)
+// Gauss-Legendre rule of n points on [-1, 1] into the caller's arrays (no allocation)
+void gauss_legendre_rule(int n, double* x, double* w);
 int build_plan(const dgfs_plan_desc* d, Plan& p);
 int upload_plan(Plan& p);
 void free_plan(Plan& p);

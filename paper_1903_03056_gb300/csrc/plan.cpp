@@ -22,10 +22,9 @@ static bool supported_n(int N) {
 size_t real_size(const Plan& p) { return p.precision == DGFS_FP32 ? sizeof(float) : sizeof(double); }
 
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the three-term
-// recurrence of P_n, w = 2 / ((1 - x^2) P_n'(x)^2).
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
+// recurrence of P_n, w = 2 / ((1 - x^2) P_n'(x)^2).  Writes n values into x and w (caller's
+// arrays; no allocation, so the allocation-free entry point uses it too).
+void gauss_legendre_rule(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
     double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
     double dp = 1.0;
@@ -54,6 +53,12 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
     x[i] = z;
     w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
   }
+}
+
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  gauss_legendre_rule(n, x.data(), w.data());
 }
 
 // Gauss-Jacobi rule for the weight (1 + t)^beta on [-1, 1] (Golub-Welsch): the nodes are the
@@ -327,6 +332,24 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
       p.w_rho_p[size_t(o) * p.N_rho + q] = 0.5 * p.pair_R[o] * w[q];
     }
   }
+  // Size of the Gauss-Jacobi rule in t of the VSS gain weight (F after Eq. GG, "precomputed
+  // to high accuracy"): the integrand's bandwidth grows with the largest argument
+  // a = pi rho c_j |k| / L over the table (largest rho node, |k| = sqrt(3) N / 2).  A
+  // 64-point rule agrees with the converged integral to 1e-13 of its bound 2^alpha / alpha
+  // up to a = 80; beyond, the size grows linearly with a (0.6 a + 14 points were measured
+  // to converge; 0.75 a + 16 rounded up to a multiple of 32 keeps a margin).
+  {
+    double a_max = 0.0;
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) {
+        const int o = i * s + j;
+        const double cj = p.mass[j] / (p.mass[i] + p.mass[j]);
+        for (int q = 0; q < p.N_rho; ++q)
+          a_max = std::max(a_max, kPi * p.rho_p[size_t(o) * p.N_rho + q] * cj * std::sqrt(3.0) * 0.5 * p.N / p.L);
+      }
+    p.vss_a_max = a_max;
+    p.n_t = a_max <= 80.0 ? 64 : 32 * int(std::ceil((0.75 * a_max + 16.0) / 32.0));
+  }
 
   // antipodal partner of every direction (equal weights required for the pair reuse)
   const int M = p.M;
@@ -577,8 +600,8 @@ int upload_plan(Plan& p) {
       return rc;
   } else {
     // VSS gain weights: prefactor w_q 2 pi b rho^(4-2 omega) / N^3 and the scale of a per
-    // (pair, rho); a 64-point Gauss-Jacobi rule per pair; representatives of antipodal pairs
-    const int n_t = 64;
+    // (pair, rho); a Gauss-Jacobi rule of p.n_t points per pair; representatives of antipodal pairs
+    const int n_t = p.n_t;
     std::vector<double> vcoef(size_t(P) * NR * 2), gj(size_t(P) * 3 * n_t);
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j) {

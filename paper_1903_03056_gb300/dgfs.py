@@ -39,7 +39,7 @@ EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
            "dgfs_plan_launches", "dgfs_plan_check", "dgfs_strerror", "dgfs_eval_collision_noalloc",
            "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step", "dgfs_dg_create", "dgfs_dg_destroy",
-           "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step")
+           "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step", "dgfs_measure_fma_rate")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -93,6 +93,7 @@ def load():
     lib.dgfs_dg_nodes.argtypes = [vp, _dptr]
     lib.dgfs_dg_transport.argtypes = [vp, vp, vp, vp]
     lib.dgfs_dg_step.argtypes = [vp, vp, ctypes.c_double, vp]
+    lib.dgfs_measure_fma_rate.argtypes = [ci, _dptr]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -196,6 +197,14 @@ def dgfs_eval_collision_noalloc(desc, f_dev, Q_dev, batch, stream):
 def _arr(x, n):
     a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (n,)).copy())
     return a, a.ctypes.data_as(_dptr)
+
+
+def dgfs_measure_fma_rate(precision):
+    """(code, flop/s) of the current device's FP32 or FP64 multiply-add pipe."""
+    out = ctypes.c_double(0.0)
+    code = load().dgfs_measure_fma_rate(DGFS_FP32 if precision in ("fp32", DGFS_FP32) else DGFS_FP64,
+                                        ctypes.byref(out))
+    return code, out.value
 
 
 def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision="fp32",

@@ -38,6 +38,7 @@ int main() {
   if (rc == DGFS_OK) {
     std::printf(", \"R\": %.17g, \"vss\": %d, \"antipodal\": %d, \"n_fslot\": %d, \"max_ent\": %d", p.R,
                 p.vss ? 1 : 0, p.antipodal ? 1 : 0, p.n_fslot, p.max_ent);
+    std::printf(", \"n_t\": %d, \"vss_a_max\": %.17g", p.n_t, p.vss_a_max);
     std::printf(", \"fslot\": [");
     for (size_t k = 0; k < p.fslot.size(); ++k) std::printf("%s%d", k ? ", " : "", p.fslot[k]);
     std::printf("], \"sigma\": [");

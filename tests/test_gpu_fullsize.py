@@ -2,7 +2,7 @@
 
 * 4096-node N=32^3 batch (the bench workload) and 16384-node N=24^3 hard-sphere batch:
   sampled nodes (first, second, middle, last) against the oracle one by one, plus finite
-  output.
+  output; FP32 and FP64 paths, each on the whole batch.
 * 1024-node N=48^3 three-species VSS batch: the oracle's VSS gain table alone would take
   tens of minutes per node at this size, so it is checked through properties that hold at
   any size.  The FP32 batch agrees with the FP64 path on sampled nodes (the FP64 VSS path is
@@ -60,6 +60,7 @@ def _eval(w, f, precision, nodes=None):
     ("dg_batch_n32", "fp32", [0, 1, 2047, 4095]),
     ("dg_batch_n32", "fp64", [0, 4095]),
     ("hs_n24", "fp32", [0, 1, 8191, 16383]),
+    ("hs_n24", "fp64", [0, 16383]),
 ])
 def test_full_batch_sampled_nodes(key, precision, nodes):
     import torch

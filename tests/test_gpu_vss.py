@@ -42,6 +42,24 @@ def test_vss_parity_with_oracle(name, precision):
     assert check(Q, ref, precision)
 
 
+_N48 = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vss_n48_parity_with_oracle(precision):
+    """One node of the N = 48 VSS grid (L = 8, masses 1 : 2.6, alpha = 1.4) against the
+    oracle.  With N_rho = 2 the outer radial node reaches a = pi rho c_j |k| / L ~ 51 at the
+    corner modes, where the t rule of F must be converged (the oracle doubles its rule until
+    it is; the plan sizes its rule from the largest argument).  The oracle's gain tables take
+    about a minute here, so its result is shared by both precisions."""
+    kw = dict(N=48, L=8.0, masses=(1.0, 2.6), omega=0.74, alpha=1.4, M=6, N_rho=2)
+    if "f" not in _N48:
+        _N48["f"] = _inputs(48, 8.0, (1.0, 2.6), 1, seed=148)
+        _N48["ref"] = oracle_collision(_N48["f"], **kw)
+    Q = gpu_collision(_N48["f"], precision=precision, **kw)
+    assert check(Q, _N48["ref"], precision)
+
+
 def test_vss_mixed_alpha_per_pair():
     """alpha may differ per pair; alpha_ij = 1 pairs then go through the same sigma-dependent
     path and must agree with the VHS closed form the oracle uses for them."""

@@ -144,6 +144,79 @@ def test_vss_gain_weight_at_antipode_is_conjugate():
     assert np.max(np.abs(anti - np.conj(at))) < 1e-12 * np.max(np.abs(at))
 
 
+def _largest_vss_argument_cfg3():
+    """The largest a = pi rho c_j |k| / L of the N = 48 three-species VSS workload (L = 8,
+    masses 1 : 1.5 : 2.6, common truncation rho <= R of Eq. domain): the corner mode
+    |k| = sqrt(3) N / 2, rho = R and the heaviest partner's c_j."""
+    masses, L, N = (1.0, 1.5, 2.6), 8.0, 48
+    R = 2.0 * kernel.support_radius(L, masses)
+    cj = max(mj / (mi + mj) for mi in masses for mj in masses)
+    return R, cj, L, np.sqrt(3.0) * N / 2
+
+
+def _modes_at_norm(kn, n_dir, seed):
+    """n_dir wave vectors of norm kn spread over the sphere (the first along a design axis)."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n_dir, 3))
+    d[0] = [0.0, 0.0, 1.0]
+    return kn * d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def test_vss_gain_weight_converged_at_largest_argument_alpha_2():
+    """At the largest argument of the N = 48 VSS workload (a ~ 65) the converged t rule meets
+    the alpha = 2 closed form 4 pi b rho^(4-2 omega) (j0(a) - i cos(theta) j1(a)) to 1e-13 of
+    the integral's bound (F "to high accuracy", Sec. 4).  A 48-point rule misses it by more
+    than 1e-11 of the bound, so a rule sized for small arguments fails here."""
+    R, cj, L, kn = _largest_vss_argument_cfg3()
+    b, omega = 0.09, 0.74
+    sigma = np.array([0.36, -0.48, 0.8])
+    k = _modes_at_norm(kn, 24, 11)
+    a = np.pi * R * cj * kn / L
+    assert a > 65.0
+    cos_t = k @ sigma / kn
+    ref = 4 * np.pi * b * R ** (4 - 2 * omega) * (np.sin(a) / a - 1j * cos_t * (np.sin(a) / a ** 2 - np.cos(a) / a))
+    bound = 2 * np.pi * b * R ** (4 - 2 * omega) * 2.0 ** 2 / 2.0
+    got = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], R, sigma, cj, b, omega, 2.0, L)
+    assert np.max(np.abs(got - ref)) < 1e-13 * bound
+    coarse = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], R, sigma, cj, b, omega, 2.0, L, n_t=48)
+    assert np.max(np.abs(coarse - ref)) > 1e-11 * bound
+
+
+def test_vss_gain_weight_converged_at_largest_argument_brute_force():
+    """The same argument at alpha = 1.4 (the VSS workload's value): the converged J0 form
+    against the brute-force product rule over g_hat (Gauss-Jacobi in t x trapezoid in phi on
+    the plane wave itself, no Bessel function) with 160 x 256 points, and against the same
+    form with a doubled rule; each to 1e-13 of the integral's bound."""
+    R, cj, L, kn = _largest_vss_argument_cfg3()
+    b, omega, alpha = 0.09, 0.74, 1.4
+    sigma = np.array([0.0, 0.6, 0.8])
+    k = _modes_at_norm(kn, 16, 12)
+    bound = 2 * np.pi * b * R ** (4 - 2 * omega) * 2.0 ** alpha / alpha
+    got = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], R, sigma, cj, b, omega, alpha, L)
+    n_conv = kernel.jacobi_rule_size(np.pi * R * cj * kn / L, alpha)
+    doubled = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], R, sigma, cj, b, omega, alpha, L, n_t=2 * n_conv)
+    brute = direct.gain_weight_by_quadrature(k, R, sigma, cj, b, omega, alpha, L, 160, 256)
+    assert np.max(np.abs(got - doubled)) < 1e-13 * bound
+    assert np.max(np.abs(got - brute)) < 1e-13 * bound
+
+
+def test_vss_rule_size_grows_with_the_argument():
+    """The doubling stops later for larger arguments, and the rule it returns agrees with a
+    rule twice its size at that argument."""
+    sizes = [kernel.jacobi_rule_size(a, 1.4) for a in (10.0, 65.0, 150.0)]
+    assert sizes[0] <= sizes[1] < sizes[2]
+    rng = np.random.default_rng(13)
+    k = _modes_at_norm(1.0, 12, 14)
+    sigma = rng.normal(size=3)
+    sigma /= np.linalg.norm(sigma)
+    for a, n in zip((10.0, 65.0, 150.0), sizes):
+        # rho c_j / L chosen so that |k| = 1 reaches the argument a
+        scale = a / np.pi
+        f1 = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], 1.0, sigma, scale, 1.0, 1.0, 1.4, 1.0, n_t=n)
+        f2 = kernel.gain_weight(k[:, 0], k[:, 1], k[:, 2], 1.0, sigma, scale, 1.0, 1.0, 1.4, 1.0, n_t=2 * n)
+        assert np.max(np.abs(f1 - f2)) < 1e-13 * 2 * np.pi * 2 ** 1.4 / 1.4
+
+
 def test_vss_gain_weight_reduces_to_vhs():
     k = np.array([[0., 0., 0.], [1., 2., 3.], [-4., 1., 0.]])
     sigma = np.array([0.0, 0.6, 0.8])

@@ -160,3 +160,23 @@ def test_invalid_descriptions_fail_in_the_builder(probe):
     assert probe(N=10)["rc"] == -2
     assert probe(omega=0.3)["rc"] == -1
     assert probe(flags=8, R=3.0)["rc"] == -1
+
+
+@pytest.mark.parametrize("R", [0.0, 12.0])
+def test_vss_rule_size_converges_at_the_plans_largest_argument(probe, R):
+    """The plan sizes the t rule of the VSS gain weight from the table's largest argument
+    a = pi rho c_j |k| / L.  On the N = 48 three-species workload (a ~ 65) it keeps 64 points;
+    a user radius of 12 pushes a past 140 and the rule grows.  At that argument and at every
+    angle, the plan's rule agrees with the oracle's converged integral to 1e-13 of the bound."""
+    from oracle import kernel
+    p = probe(N=48, L=8.0, masses=(1.0, 1.5, 2.6), omega=0.74, alpha=1.4, M=32, N_rho=24, R=R)
+    assert p["rc"] == 0 and p["vss"] == 1
+    a = p["vss_a_max"]
+    if R == 0.0:
+        assert 60.0 < a < 65.3 and p["n_t"] == 64
+    else:
+        assert a > 140.0 and p["n_t"] > 64
+    cos_t = np.linspace(-1.0, 1.0, 21)
+    plan_rule = kernel.phi_integral(a, cos_t, 1.4, p["n_t"])
+    converged = kernel.phi_integral(a, cos_t, 1.4, kernel.jacobi_rule_size(a, 1.4))
+    assert np.max(np.abs(plan_rule - converged)) < 1e-13 * 2 ** 1.4 / 1.4

@@ -19,7 +19,7 @@
  *             points depends only on the sampled values of f, not on this offset.
  * Layouts   : f[batch][s][N][N][N] and Q[batch][s][s][N][N][N] (x slowest, z fastest),
  *             Q[b][i][j] = Q_ij(f_i, f_j) at node b.  Element type: double for DGFS_FP64
- *             plans, float for DGFS_FP32 plans.
+ *             plans, float for DGFS_FP32 and DGFS_BF16X3 plans.
  * Ownership : the caller owns f and Q.  f is only read; every element of Q is written.
  *             The plan owns its tables and its workspace (device memory on the device that
  *             was current at dgfs_create_plan).
@@ -51,13 +51,20 @@ extern "C" {
 #define DGFS_ERR_OOM (-3)            /* device or host allocation failed */
 #define DGFS_ERR_BUDGET (-4)         /* batch larger than the plan's max_batch */
 #define DGFS_ERR_CUDA (-5)           /* a CUDA runtime call or kernel launch failed */
-#define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up (reserved: the
-                                        kernels of this build have no device-side waits) */
+#define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up: the DGFS_BF16X3
+                                        kernel waits at most about one second for each batch
+                                        of its tensor-core MMAs, then stops and records it;
+                                        reported by dgfs_plan_check and dgfs_dft3_bf16x3 */
 #define DGFS_ERR_UNSUPPORTED (-7)    /* a valid request this build does not implement */
 
 /* arithmetic of the transforms, products and accumulations */
 #define DGFS_FP64 0
 #define DGFS_FP32 1
+#define DGFS_BF16X3 2 /* the transforms as dense matrix products on the tensor cores: every FP32
+                         operand split exactly into three BF16 terms, the six products of order
+                         down to 2^-16 accumulated in FP32 (f and Q in float, like DGFS_FP32).
+                         VHS only (alpha = 1), N in {8, 16, 24}; else DGFS_ERR_UNSUPPORTED or
+                         DGFS_ERR_UNSUPPORTED_N at plan creation */
 
 /* plan flags */
 #define DGFS_CONSERVE 1u    /* project each self pair and each stacked cross pair onto the
@@ -93,7 +100,7 @@ typedef struct {
   const double* w_sigma;   /* nullable [M]: its weights (default 4 pi / M each) */
   int N_rho;               /* Gauss-Legendre points in rho on [0, R], >= 1 */
   double R;                /* radial truncation; <= 0 selects R = 2S with S from Eq. domain */
-  int precision;           /* DGFS_FP64 or DGFS_FP32 */
+  int precision;           /* DGFS_FP64, DGFS_FP32 or DGFS_BF16X3 */
   unsigned flags;          /* 0 or DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE |
                               DGFS_PER_PAIR_R */
   int max_batch;           /* largest batch of a host-buffer call or of a DGFS_SUM_SPECIES plan */
@@ -167,7 +174,9 @@ int dgfs_plan_set_sm_share(dgfs_plan plan, double share);
  * plan's most recent evaluation (waited for on the plan's own stream; evaluations recorded
  * into a CUDA graph must have completed before the call), both blocks are read back and
  * *intact = 1 when every byte still holds the pattern, 0 when a kernel wrote outside the
- * workspace.  Errors: DGFS_ERR_INVALID_ARG (null plan or pointer), DGFS_ERR_CUDA. */
+ * workspace.  Returns DGFS_ERR_DEVICE_TIMEOUT (with *intact set) when a kernel of the plan
+ * recorded that one of its bounded device-side waits gave up.  Errors: DGFS_ERR_INVALID_ARG
+ * (null plan or pointer), DGFS_ERR_CUDA. */
 int dgfs_plan_check(dgfs_plan plan, int* intact);
 
 /* Kernels enqueued by the most recent evaluation on this plan. */
@@ -175,6 +184,18 @@ int dgfs_plan_launches(dgfs_plan plan, int* launches);
 
 /* Static text naming a return code. */
 const char* dgfs_strerror(int code);
+
+/* Batched 3D discrete Fourier transform on the tensor cores, the building block of the
+ * DGFS_BF16X3 path (the truncated Fourier series of Sec. 4 and its coefficients are such
+ * transforms on the N^3 grid):  y_v[n] = sum_k x_v[k] e^{dir 2 pi i k.n / N}, unnormalised,
+ * for v = 0..count-1.  x_dev and y_dev: [count][N][N][N] complex float (interleaved re, im),
+ * device memory, 16-byte aligned, not overlapping; N in {8, 16, 24} (else
+ * DGFS_ERR_UNSUPPORTED_N); dir = -1 (forward) or +1 (inverse), else DGFS_ERR_INVALID_ARG.  Each
+ * axis is one pass of tensor-core matrix products with every FP32 operand split into three BF16
+ * terms (as DGFS_BF16X3).  Allocates a 14 KB matrix image stream-ordered on `stream`, runs, and
+ * returns when done (synchronises `stream`); DGFS_ERR_DEVICE_TIMEOUT when the kernel's bounded
+ * wait for its MMAs gave up. */
+int dgfs_dft3_bf16x3(int N, int dir, const void* x_dev, void* y_dev, int count, void* stream);
 
 /* Measured multiply-add rate of the current device's FP32 (precision = DGFS_FP32) or FP64
  * (DGFS_FP64) pipe, in flop/s (2 flop per FMA): the denominator of the ALU roofline that bounds

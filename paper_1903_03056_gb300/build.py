@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgfs.so")
 
 SOURCES = ["api.cpp", "plan.cpp", "collision_f32.cu", "collision_f64.cu", "collision_noalloc.cu", "conserve.cu", "tables.cu",
-           "stepper.cu", "dg1d.cu", "peaks.cu"]
+           "stepper.cu", "dg1d.cu", "peaks.cu", "dft_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

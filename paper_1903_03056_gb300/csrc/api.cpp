@@ -44,8 +44,9 @@ int launch(dgfs::Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
   const bool sum = (p.flags & DGFS_SUM_SPECIES) != 0u;
   if (sum && (batch > p.max_batch || !p.d_Qfull)) return DGFS_ERR_BUDGET;
   void* Qfull = sum ? p.d_Qfull : Q;
-  int rc = p.precision == DGFS_FP32 ? dgfs::launch_f32(p, f, Qfull, batch, st)
-                                    : dgfs::launch_f64(p, f, Qfull, batch, st);
+  int rc = p.precision == DGFS_FP32     ? dgfs::launch_f32(p, f, Qfull, batch, st)
+           : p.precision == DGFS_BF16X3 ? dgfs::launch_bf16x3(p, f, Qfull, batch, st)
+                                        : dgfs::launch_f64(p, f, Qfull, batch, st);
   if (rc != DGFS_OK) return rc;
   p.last_launches = 1;
   if (p.flags & DGFS_CONSERVE) {
@@ -83,7 +84,10 @@ int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out) {
   dgfs::Plan& p = h->plan;
   int rc = dgfs::build_plan(desc, p);
   if (rc == DGFS_OK && cudaGetDevice(&p.device) != cudaSuccess) rc = DGFS_ERR_CUDA;
-  if (rc == DGFS_OK) rc = p.precision == DGFS_FP32 ? dgfs::configure_f32(p) : dgfs::configure_f64(p);
+  if (rc == DGFS_OK)
+    rc = p.precision == DGFS_FP32     ? dgfs::configure_f32(p)
+         : p.precision == DGFS_BF16X3 ? dgfs::configure_bf16x3(p)
+                                      : dgfs::configure_f64(p);
   if (rc == DGFS_OK) rc = dgfs::upload_plan(p);
   if (rc != DGFS_OK) {
     dgfs::free_plan(p);
@@ -265,7 +269,14 @@ int dgfs_plan_check(dgfs_plan plan, int* intact) {
   int ok = 1;
   for (size_t k = 0; k < 2 * G; ++k) ok &= host[k] == dgfs::Plan::kGuardByte ? 1 : 0;
   *intact = ok;
-  return DGFS_OK;
+  // the device status word beside the work counter: a bounded device-side wait gave up
+  unsigned status = 0;
+  if (cudaMemcpyAsync(&status, p.d_counter + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, p.home) != cudaSuccess ||
+      cudaStreamSynchronize(p.home) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  return status != 0 ? DGFS_ERR_DEVICE_TIMEOUT : DGFS_OK;
 }
 
 int dgfs_plan_launches(dgfs_plan plan, int* launches) {

@@ -119,7 +119,7 @@ int launch_conserve(const Plan& p, void* Q, int batch, cudaStream_t st) {
   const int nb = int(p.cons.size());
   if (nb == 0 || batch == 0) return DGFS_OK;
   const dim3 grid(unsigned(batch) * nb);
-  if (p.precision == DGFS_FP32)
+  if (p.f32io())
     conserve_kernel<float><<<grid, kConsThreads, 0, st>>>(static_cast<float*>(Q), p.s, p.N, p.L, p.d_cons, nb);
   else
     conserve_kernel<double><<<grid, kConsThreads, 0, st>>>(static_cast<double*>(Q), p.s, p.N, p.L, p.d_cons, nb);
@@ -132,7 +132,7 @@ int launch_species_sum(const Plan& p, const void* Qfull, void* Qsum, int batch, 
   const unsigned gx = unsigned((N3 + 255) / 256 < 64 ? (N3 + 255) / 256 : 64);
   const unsigned gy = unsigned(batch) * p.s < 65535u ? unsigned(batch) * p.s : 65535u;
   const dim3 grid(gx, gy);
-  if (p.precision == DGFS_FP32)
+  if (p.f32io())
     species_sum_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(Qfull), static_cast<float*>(Qsum),
                                                     batch, p.s, N3, p.d_kappa);
   else

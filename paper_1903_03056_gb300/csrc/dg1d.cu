@@ -305,7 +305,7 @@ int launch_transport(dgfs_dg_plan_s& d, int mode, const void* F, const void* F0,
 
 int transport(dgfs_dg_plan_s& d, int mode, const void* F, const void* F0, const void* C, void* out, double dt,
               cudaStream_t st) {
-  return d.coll->plan.precision == DGFS_FP32 ? launch_transport<float>(d, mode, F, F0, C, out, dt, st)
+  return d.coll->plan.f32io() ? launch_transport<float>(d, mode, F, F0, C, out, dt, st)
                                              : launch_transport<double>(d, mode, F, F0, C, out, dt, st);
 }
 
@@ -427,7 +427,7 @@ int dgfs_dg_create(const dgfs_dg_desc* desc, dgfs_plan collision, dgfs_dg_plan* 
       }
     }
   }
-  const size_t esz = p.precision == DGFS_FP32 ? sizeof(float) : sizeof(double);
+  const size_t esz = p.f32io() ? sizeof(float) : sizeof(double);
   const size_t state = size_t(d->B) * p.s * N3 * esz;
   if (cudaMalloc(&d->d_W, Wd.size() * esz) != cudaSuccess || cudaMalloc((void**)&d->d_num, 2 * kMaxS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&d->d_F1, state) != cudaSuccess || cudaMalloc(&d->d_C, state) != cudaSuccess) {
@@ -436,7 +436,7 @@ int dgfs_dg_create(const dgfs_dg_desc* desc, dgfs_plan collision, dgfs_dg_plan* 
     return DGFS_ERR_OOM;
   }
   cudaError_t ce;
-  if (p.precision == DGFS_FP32) {
+  if (p.f32io()) {
     std::vector<float> Wf(Wd.begin(), Wd.end());
     ce = cudaMemcpy(d->d_W, Wf.data(), Wf.size() * sizeof(float), cudaMemcpyHostToDevice);
   } else {

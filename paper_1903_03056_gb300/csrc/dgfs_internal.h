@@ -2,7 +2,9 @@
 // kernel launchers and the C ABI.
 #pragma once
 
+#include <complex>
 #include <cstddef>
+#include <cstdint>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -90,6 +92,8 @@ struct Plan {
   int N_rho = 0;
   double R = 0;
   int precision = DGFS_FP64;
+  // f and Q in float: the FP32 path and the split-BF16 tensor-core path
+  bool f32io() const { return precision != DGFS_FP64; }
   unsigned flags = 0;
   int max_batch = 0;
   std::vector<double> mass, omega, alpha, b, sigma, w_sigma, rho, w_rho;
@@ -137,7 +141,9 @@ struct Plan {
   void* d_scratch_raw = nullptr;   // guard | workspace | guard
   static constexpr size_t kGuardBytes = 4096;
   static constexpr unsigned char kGuardByte = 0xA5;
-  unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel
+  unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel; the next word is
+                                   // the device status (set when a bounded device wait gave up)
+  uint16_t* d_mats = nullptr;      // DGFS_BF16X3: line-transform matrix images (split BF16)
   size_t scratch_bytes = 0;
   void* d_rk = nullptr;             // SSP-RK2 workspace: f1 and the right-hand side
   void* d_stage_f = nullptr;
@@ -185,6 +191,13 @@ int launch_gain_tables_f32(Plan& p, int self_sum);
 int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps);
+
+// split-BF16 tensor-core path (dft_gemm.cu): N it supports, matrix images from the plan's
+// phase factors [task][rho][max_ent][role][axis][N], kernel configuration and launch
+bool gemm_supported_n(int N);
+void build_gemm_images(const Plan& p, const std::vector<std::complex<double>>& phase, std::vector<uint16_t>& out);
+int configure_bf16x3(Plan& p);
+int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
 
 // SSP-RK2 stage combinations (stepper.cu): stage 1 f1 = f + dt r; stage 2 f = (f + f1 + dt r)/2
 int launch_rk_stage(const Plan& p, int stage, void* f, void* f1, const void* r, double dt, size_t n, cudaStream_t st);

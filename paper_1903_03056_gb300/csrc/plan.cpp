@@ -19,7 +19,7 @@ static bool supported_n(int N) {
   }
 }
 
-size_t real_size(const Plan& p) { return p.precision == DGFS_FP32 ? sizeof(float) : sizeof(double); }
+size_t real_size(const Plan& p) { return p.f32io() ? sizeof(float) : sizeof(double); }
 
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the three-term
 // recurrence of P_n, w = 2 / ((1 - x^2) P_n'(x)^2).  Writes n values into x and w (caller's
@@ -249,7 +249,7 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
   if (!supported_n(d->N)) return DGFS_ERR_UNSUPPORTED_N;
   if (!(d->L > 0.0) || d->s < 1 || d->s > 8 || !d->mass || !d->omega || !d->alpha) return DGFS_ERR_INVALID_ARG;
   if (d->N_rho < 1 || d->N_rho > 4096 || d->M < 1 || d->max_batch < 0) return DGFS_ERR_INVALID_ARG;
-  if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32) return DGFS_ERR_INVALID_ARG;
+  if (d->precision != DGFS_FP64 && d->precision != DGFS_FP32 && d->precision != DGFS_BF16X3) return DGFS_ERR_INVALID_ARG;
   if ((d->flags & ~(DGFS_CONSERVE | DGFS_SUM_SPECIES | DGFS_LOSS_ACCURATE | DGFS_PER_PAIR_R)) != 0u)
     return DGFS_ERR_INVALID_ARG;
   if ((d->flags & DGFS_PER_PAIR_R) && d->R > 0.0) return DGFS_ERR_INVALID_ARG;
@@ -270,6 +270,11 @@ int build_plan(const dgfs_plan_desc* d, Plan& p) {
     if (!(p.omega[k] >= 0.5 && p.omega[k] <= 1.0)) return DGFS_ERR_INVALID_ARG;
     if (!(p.alpha[k] >= 1.0 && p.alpha[k] <= 2.0)) return DGFS_ERR_INVALID_ARG;
     if (p.alpha[k] != 1.0) p.vss = true;
+  }
+  // the tensor-core path evaluates the sigma-independent (VHS) gain weight on N <= 24
+  if (p.precision == DGFS_BF16X3) {
+    if (!gemm_supported_n(p.N)) return DGFS_ERR_UNSUPPORTED_N;
+    if (p.vss) return DGFS_ERR_UNSUPPORTED;
   }
   p.kappa.assign(s * s, 1.0);
   if (d->kappa)
@@ -555,7 +560,9 @@ int upload_plan(Plan& p) {
   }
   std::vector<float> phf;
   std::vector<double> phd;
-  if (p.precision == DGFS_FP32) {
+  std::vector<uint16_t> mats;
+  if (p.precision == DGFS_BF16X3) build_gemm_images(p, ph, mats);
+  if (p.f32io()) {
     phf.resize(2 * nph);
     for (size_t n = 0; n < nph; ++n) {
       phf[2 * n] = float(ph[n].real());
@@ -637,7 +644,7 @@ int upload_plan(Plan& p) {
     if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale), NL))) return rc;
     if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
   }
-  if (p.precision == DGFS_FP32) {
+  if (p.f32io()) {
     // the FP32 kernel reads FP32 gain tables: each FP64 value rounded once here instead of
     // converted per element in the kernel (GB300's FP64 rate is a small fraction of its FP32
     // rate); with an antipodal design a self pair's slots take F(sigma) + F(-sigma) =
@@ -669,7 +676,8 @@ int upload_plan(Plan& p) {
   if ((rc = upload(p, p.tasks.data(), p.tasks.size(), (void**)&p.d_tasks, total))) return rc;
   if ((rc = upload(p, p.groups.data(), p.groups.size(), (void**)&p.d_groups, total))) return rc;
   if ((rc = upload(p, p.ent_ysh.data(), p.ent_ysh.size(), (void**)&p.d_ent_ysh, total))) return rc;
-  if (p.precision == DGFS_FP32) {
+  if (!mats.empty() && (rc = upload(p, mats.data(), mats.size(), (void**)&p.d_mats, total))) return rc;
+  if (p.f32io()) {
     if ((rc = upload(p, phf.data(), phf.size(), &p.d_phase, total))) return rc;
   } else {
     if ((rc = upload(p, phd.data(), phd.size(), &p.d_phase, total))) return rc;
@@ -691,6 +699,11 @@ int upload_plan(Plan& p) {
     return DGFS_ERR_CUDA;
   }
   if ((rc = dalloc(p, (void**)&p.d_counter, 256))) return rc;
+  // work counter and device status word start at zero
+  if (cudaMemsetAsync(p.d_counter, 0, 256, p.home) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
   // the host arrays above must outlive the copies
   if (cudaStreamSynchronize(p.home) != cudaSuccess) return DGFS_ERR_CUDA;
   return DGFS_OK;
@@ -699,7 +712,7 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch_raw, p.d_stage_f, p.d_stage_Q, p.d_cons, p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf};
+                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf,   p.d_mats};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -736,6 +749,7 @@ void free_plan(Plan& p) {
   p.d_ent_ysh = nullptr;
   p.d_counter = nullptr;
   p.d_rk = nullptr;
+  p.d_mats = nullptr;
 }
 
 }  // namespace dgfs

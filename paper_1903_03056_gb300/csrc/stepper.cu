@@ -27,7 +27,7 @@ unsigned blocks_for(size_t n) { return unsigned(n / 256 + 1 < 8192 ? n / 256 + 1
 }  // namespace
 
 int launch_rk_stage(const Plan& p, int stage, void* f, void* f1, const void* r, double dt, size_t n, cudaStream_t st) {
-  if (p.precision == DGFS_FP32) {
+  if (p.f32io()) {
     if (stage == 1)
       rk_stage1<float><<<blocks_for(n), 256, 0, st>>>(static_cast<const float*>(f), static_cast<const float*>(r),
                                                       static_cast<float*>(f1), float(dt), n);

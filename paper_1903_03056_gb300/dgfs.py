@@ -26,6 +26,7 @@ DGFS_ERR_DEVICE_TIMEOUT = -6
 DGFS_ERR_UNSUPPORTED = -7
 DGFS_FP64 = 0
 DGFS_FP32 = 1
+DGFS_BF16X3 = 2
 DGFS_CONSERVE = 1
 DGFS_SUM_SPECIES = 2
 DGFS_LOSS_ACCURATE = 4
@@ -39,7 +40,8 @@ EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_eval_collision_host", "dgfs_plan_bytes", "dgfs_plan_radius",
            "dgfs_plan_launches", "dgfs_plan_check", "dgfs_strerror", "dgfs_eval_collision_noalloc",
            "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step", "dgfs_dg_create", "dgfs_dg_destroy",
-           "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step", "dgfs_measure_fma_rate")
+           "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step", "dgfs_measure_fma_rate",
+           "dgfs_dft3_bf16x3")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -94,6 +96,7 @@ def load():
     lib.dgfs_dg_transport.argtypes = [vp, vp, vp, vp]
     lib.dgfs_dg_step.argtypes = [vp, vp, ctypes.c_double, vp]
     lib.dgfs_measure_fma_rate.argtypes = [ci, _dptr]
+    lib.dgfs_dft3_bf16x3.argtypes = [ci, ci, vp, vp, ci, vp]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -207,6 +210,20 @@ def dgfs_measure_fma_rate(precision):
     return code, out.value
 
 
+def precision_code(precision):
+    """"fp64" / "fp32" / "bf16x3" (or the DGFS_* code itself) -> the DGFS_* code."""
+    names = {"fp64": DGFS_FP64, "fp32": DGFS_FP32, "bf16x3": DGFS_BF16X3}
+    if precision in names:
+        return names[precision]
+    if precision in (DGFS_FP64, DGFS_FP32, DGFS_BF16X3):
+        return int(precision)
+    raise ValueError("unknown precision %r" % (precision,))
+
+
+def dgfs_dft3_bf16x3(N, direction, x_dev, y_dev, count, stream):
+    return load().dgfs_dft3_bf16x3(N, direction, x_dev, y_dev, count, _stream_handle(stream))
+
+
 def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision="fp32",
               b_override=None, sigma=None, w_sigma=None, max_batch=0, flags=0, kappa=None):
     """Build a dgfs_plan_desc; returns (desc, keepalive) -- keep the second alive until the
@@ -236,7 +253,7 @@ def make_desc(N, L, masses, omega, alpha=1.0, M=12, N_rho=None, R=0.0, precision
     d.M = int(M)
     d.N_rho = int(N if N_rho is None else N_rho)
     d.R = float(R)
-    d.precision = DGFS_FP32 if precision in ("fp32", DGFS_FP32) else DGFS_FP64
+    d.precision = precision_code(precision)
     d.flags = int(flags)
     d.max_batch = int(max_batch)
     if kappa is not None:
@@ -255,7 +272,7 @@ def _stream_handle(stream):
 
 
 class Plan:
-    """Owns one dgfs plan.  ``precision`` is "fp32" or "fp64"."""
+    """Owns one dgfs plan.  ``precision`` is "fp32", "fp64" or "bf16x3"."""
 
     def __init__(self, N, L, masses, omega, **kw):
         desc, keep = make_desc(N, L, masses, omega, **kw)
@@ -270,7 +287,7 @@ class Plan:
 
     @property
     def dtype_name(self):
-        return "float32" if self.precision in ("fp32", DGFS_FP32) else "float64"
+        return "float64" if precision_code(self.precision) == DGFS_FP64 else "float32"
 
     def radius(self):
         code, r = dgfs_plan_radius(self.handle)

@@ -14,7 +14,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="dg_batch_n32")
     ap.add_argument("--batch", type=int, default=None)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--checksum", action="store_true", help="add the SHA-1 of the output bytes")
     ap.add_argument("--n-rho", type=int, default=None,
@@ -32,7 +32,7 @@ def main():
         w = dataclasses.replace(w, N_rho=a.n_rho)
     B = a.batch or w.batch
     f = synth.batch_distribution(w, nodes=range(B))
-    dt = torch.float32 if a.precision == "fp32" else torch.float64
+    dt = torch.float64 if a.precision == "fp64" else torch.float32
     fd = torch.from_numpy(f).to(device="cuda", dtype=dt)
     Q = torch.empty((B, w.s, w.s, w.N, w.N, w.N), dtype=dt, device="cuda")
     import time

@@ -16,7 +16,7 @@ def gpu_collision(f, *, N, L, masses, omega, M=12, N_rho=8, precision="fp64", si
                   w_sigma=None, b_override=None, R=0.0, alpha=1.0, flags=0):
     """f: numpy [B, s, N, N, N] float64 -> Q numpy [B, s, s, N, N, N] from libdgfs."""
     import torch
-    dt = torch.float32 if precision == "fp32" else torch.float64
+    dt = torch.float64 if precision == "fp64" else torch.float32
     plan = dgfs.Plan(N, L, masses, omega, alpha=alpha, M=M, N_rho=N_rho, precision=precision,
                      sigma=sigma, w_sigma=w_sigma, b_override=b_override, R=R, flags=flags)
     fd = torch.from_numpy(np.ascontiguousarray(f)).to(device="cuda", dtype=dt)

@@ -180,3 +180,14 @@ def test_vss_rule_size_converges_at_the_plans_largest_argument(probe, R):
     plan_rule = kernel.phi_integral(a, cos_t, 1.4, p["n_t"])
     converged = kernel.phi_integral(a, cos_t, 1.4, kernel.jacobi_rule_size(a, 1.4))
     assert np.max(np.abs(plan_rule - converged)) < 1e-13 * 2 ** 1.4 / 1.4
+
+
+def test_bf16x3_plans_accept_vhs_on_n_up_to_24_only(probe):
+    """The tensor-core precision (code 2) builds VHS plans on N = 8, 16, 24; other N return
+    DGFS_ERR_UNSUPPORTED_N (-2) and alpha != 1 DGFS_ERR_UNSUPPORTED (-7), before any device work."""
+    assert probe(N=24, masses=(1.0, 4.0), omega=0.5, precision=2)["rc"] == 0
+    assert probe(N=8, precision=2)["rc"] == 0
+    assert probe(N=32, precision=2)["rc"] == -2
+    assert probe(N=12, precision=2)["rc"] == -2
+    assert probe(N=16, alpha=1.4, precision=2)["rc"] == -7
+    assert probe(N=16, precision=3)["rc"] == -1

@@ -46,36 +46,52 @@ struct Vol {
 };
 
 // One 3D transform: pass 1 from `src` (writes the A rows), passes 2 and 3 by transposes
-// through shared memory, `epi` reads the result (thread t = line t of the last pass).
-// XYZ: passes along x, y, z; the result's lines are (x, y) with z along the columns.
-// ZYX: passes along z, y, x; the result's lines are (y, z) with x along the columns.
+// through shared memory, `epi` reads the result (thread t = row t of the last pass).
+// XYZ: passes along x, y, z (orders kPX, kPY, kPZ); the result's rows are kPZ lines (x, y)
+// with z along the columns.  ZYX: passes along z, y, x (kPZ, kPY2, kPX2); the result's rows
+// are kPX2 lines (y, z) with x along the columns.  Each pass's matrix is copied in (bulk copy)
+// while the previous pass runs.
 template <int N, bool ZYX, class Src, class Epi>
 __device__ __forceinline__ bool dft3(GemmCta<N>& cta, int t, const uint16_t* m0, const uint16_t* m1,
                                      const uint16_t* m2, Src&& src, Epi&& epi) {
   __syncthreads();  // workspace written by other threads' epilogues is read below
-  cta.load_matrix(m0, t);
+  cta.prefetch_matrix(m0, t);
   src(t);
-  if (!cta.mma_pass(t)) return false;
-  cta.load_matrix(m1, t);
-  if constexpr (ZYX) convert_pass<N, 2, 1>(cta, t); else convert_pass<N, 0, 1>(cta, t);
-  if (!cta.mma_pass(t)) return false;
-  cta.load_matrix(m2, t);
-  if constexpr (ZYX) convert_pass<N, 1, 0>(cta, t); else convert_pass<N, 1, 2>(cta, t);
-  if (!cta.mma_pass(t)) return false;
+  if (!cta.mma_pass(t, m1)) return false;
+  if constexpr (ZYX) convert_pass<N, kPZ, kPY2>(cta, t); else convert_pass<N, kPX, kPY>(cta, t);
+  if (!cta.mma_pass(t, m2)) return false;
+  if constexpr (ZYX) convert_pass<N, kPY2, kPX2>(cta, t); else convert_pass<N, kPY, kPZ>(cta, t);
+  if (!cta.mma_pass(t, nullptr)) return false;
   epi(t);
   return true;
 }
 
-// pass-1 source of an XYZ transform: line t = (y, z) of a volume in natural layout
+// natural index x N^2 + y N of the line (y, z) of row t of the x pass (add x N^2 for a point)
+template <int N>
+__device__ __forceinline__ int px_base(int t) {
+  int c[3];
+  line_of<N, kPX>(t, c);
+  return c[1] * N + c[2];
+}
+// natural index (x N + y) N of the line (x, y) of row t of the z pass (add z for a point)
+template <int N>
+__device__ __forceinline__ int pz_base(int t) {
+  int c[3];
+  line_of<N, kPZ>(t, c);
+  return (c[0] * N + c[1]) * N;
+}
+
+// pass-1 source of an XYZ transform: the x line of row t of a volume in natural layout
 // [x][y][z]; real (im = 0) or complex, optionally times a real table
 template <int N>
 __device__ __forceinline__ void src_real(const GemmCta<N>& cta, int t, const float* vol) {
   using G = GemmGeo<N>;
   if ((t & ~31) >= G::N2) return;
+  const int o = px_base<N>(t);
   float v[G::K];
 #pragma unroll
   for (int x = 0; x < N; ++x) {
-    v[2 * x] = __ldg(vol + x * G::N2 + t);
+    v[2 * x] = __ldg(vol + x * G::N2 + o);
     v[2 * x + 1] = 0.f;
   }
   cta.put_row(t, v);
@@ -84,12 +100,13 @@ template <int N>
 __device__ __forceinline__ void src_cplx(const GemmCta<N>& cta, int t, const float2* vol, const float* g) {
   using G = GemmGeo<N>;
   if ((t & ~31) >= G::N2) return;
+  const int o = px_base<N>(t);
   float v[G::K];
 #pragma unroll
   for (int x = 0; x < N; ++x) {
-    float2 c = vol[x * G::N2 + t];
+    float2 c = vol[x * G::N2 + o];
     if (g) {
-      const float s = __ldg(g + x * G::N2 + t);
+      const float s = __ldg(g + x * G::N2 + o);
       c.x *= s;
       c.y *= s;
     }
@@ -98,7 +115,8 @@ __device__ __forceinline__ void src_cplx(const GemmCta<N>& cta, int t, const flo
   }
   cta.put_row(t, v);
 }
-// pass-1 source of a ZYX transform: line t = (x, y) of the product sum in tensor memory
+// pass-1 source of a ZYX transform: row t of the product sum in tensor memory (kPZ order, the
+// z pass's own order)
 template <int N>
 __device__ __forceinline__ void src_tmem(const GemmCta<N>& cta, int t) {
   using G = GemmGeo<N>;
@@ -116,44 +134,57 @@ __device__ __forceinline__ void src_tmem(const GemmCta<N>& cta, int t) {
   cta.put_row(t, v);
 }
 
-// XYZ result, line t = (x, y): hand each (z, re, im) to fn
+// XYZ result, row t: hand each (natural index, re, im) of its z line to fn
 template <int N, class Fn>
 __device__ __forceinline__ void for_result(const GemmCta<N>& cta, int t, Fn&& fn) {
   using G = GemmGeo<N>;
   if ((t & ~31) >= G::N2) return;
   const uint32_t ta = cta.lane_addr(t, 0);
+  const int o = pz_base<N>(t);
 #pragma unroll 1
   for (int ch = 0; ch < G::NN / 16; ++ch) {
     float d[16];
     tc::tmem_ld16(ta + uint32_t(16 * ch), d);
     tc::tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) fn(8 * ch + j, d[2 * j], d[2 * j + 1]);
+    for (int j = 0; j < 8; ++j) fn(o + 8 * ch + j, d[2 * j], d[2 * j + 1]);
   }
 }
 
 template <int N>
-__global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(const GemmParams p) {
+__device__ __forceinline__ void init_cta(GemmCta<N>& cta, unsigned char* smem, uint64_t* bar, uint64_t* bbar, int* abort_flag,
+                                         unsigned* status, int t) {
+  using G = GemmGeo<N>;
+  cta.A = reinterpret_cast<uint16_t*>(smem);
+  cta.B = cta.A + G::A_ELEMS;
+  cta.bar = bar;
+  cta.bbar = bbar;
+  cta.abort_flag = abort_flag;
+  cta.status = status;
+  cta.phase = 0;
+  cta.bphase = 0;
+  cta.bsel = 0;
+  if (t == 0) {
+    *abort_flag = 0;
+    tc::mbar_init(bar, 1);
+    tc::mbar_init(&bbar[0], 1);
+    tc::mbar_init(&bbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(GemmGeo<N>::THREADS, GemmGeo<N>::MINB) gemm_collision_kernel(const GemmParams p) {
   using G = GemmGeo<N>;
   constexpr int N2 = G::N2, N3 = G::N3;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_bbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_item;
   const int t = threadIdx.x;
 
   GemmCta<N> cta;
-  cta.A = reinterpret_cast<uint16_t*>(smem_raw);
-  cta.B = cta.A + G::A_ELEMS;
-  cta.bar = &s_bar;
-  cta.abort_flag = &s_abort;
-  cta.status = p.status;
-  cta.phase = 0;
-  if (t == 0) {
-    s_abort = 0;
-    tc::mbar_init(&s_bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  init_cta<N>(cta, smem_raw, &s_bar, s_bbar, &s_abort, p.status, t);
   // padding rows of the A operand hold zeros (their outputs are never read)
   for (int i = t; i < G::A_ELEMS / 8; i += G::THREADS) reinterpret_cast<uint4*>(cta.A)[i] = make_uint4(0, 0, 0, 0);
   if (t < 32) {
@@ -197,8 +228,8 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
       float2* dst = sp == 0 ? V.FI : V.FJ;
       ok = dft3<N, false>(cta, t, fwd, fwd, fwd, [&](int tt) { src_real<N>(cta, tt, fs); },
                           [&](int tt) {
-                            for_result<N>(cta, tt, [&](int z, float re, float im) {
-                              dst[tt * N + z] = make_float2(re * inv_n3, im * inv_n3);
+                            for_result<N>(cta, tt, [&](int idx, float re, float im) {
+                              dst[idx] = make_float2(re * inv_n3, im * inv_n3);
                             });
                           });
     }
@@ -213,7 +244,7 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
         // a: shifted f_i, kept in the workspace (line t of the result is written and read by thread t)
         ok = dft3<N, false>(cta, t, ma, ma + img, ma + 2 * img, [&](int tt) { src_cplx<N>(cta, tt, V.FI, nullptr); },
                             [&](int tt) {
-                              for_result<N>(cta, tt, [&](int z, float re, float im) { V.AV[tt * N + z] = make_float2(re, im); });
+                              for_result<N>(cta, tt, [&](int idx, float re, float im) { V.AV[idx] = make_float2(re, im); });
                             });
         if (!ok) break;
         // b: shifted f_j; P (+)= w a b in tensor memory
@@ -222,7 +253,7 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
                             [&](int tt) {
                               if ((tt & ~31) >= N2) return;
                               const uint32_t tD = cta.lane_addr(tt, 0), tP = cta.lane_addr(tt, 1);
-                              const float2* a = V.AV + tt * N;
+                              const float2* a = V.AV + pz_base<N>(tt);
 #pragma unroll 1
                               for (int ch = 0; ch < G::NN / 16; ++ch) {
                                 float d[16], pv[16];
@@ -248,6 +279,9 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
                          [&](int tt) {
                            if ((tt & ~31) >= N2) return;
                            const uint32_t tD = cta.lane_addr(tt, 0);
+                           int c[3];
+                           line_of<N, kPX2>(tt, c);
+                           const int o = c[1] * N + c[2];
 #pragma unroll 1
                            for (int ch = 0; ch < G::NN / 16; ++ch) {
                              float d[16];
@@ -255,7 +289,7 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
                              tc::tmem_wait_ld();
 #pragma unroll
                              for (int j = 0; j < 8; ++j) {
-                               const int idx = (8 * ch + j) * N2 + tt;  // (x, y, z), line tt = (y, z)
+                               const int idx = (8 * ch + j) * N2 + o;  // (x, y, z) of the x line (y, z)
 #pragma unroll
                                for (int o = 0; o < 2; ++o) {
                                  const int pair = o == 0 ? tk.out0 : tk.out1;
@@ -284,14 +318,13 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
       const float2* acc = o == 0 ? V.QA : V.QB;
       const float2* Fj = jo == tk.i ? V.FI : FJs;
       ok = dft3<N, false>(cta, t, inv, inv, inv, [&](int tt) { src_cplx<N>(cta, tt, Fj, p.Gm + size_t(pair) * N3); },
-                          [&](int tt) { for_result<N>(cta, tt, [&](int z, float re, float) { V.LS[tt * N + z] = re; }); });
+                          [&](int tt) { for_result<N>(cta, tt, [&](int idx, float re, float) { V.LS[idx] = re; }); });
       if (!ok) break;
       float* Qo = p.Q + ((size_t(b) * p.s + io) * p.s + jo) * N3;
       const float* fi = fb + size_t(io) * N3;
       ok = dft3<N, false>(cta, t, inv, inv, inv, [&](int tt) { src_cplx<N>(cta, tt, acc, nullptr); },
                           [&](int tt) {
-                            for_result<N>(cta, tt, [&](int z, float re, float) {
-                              const int idx = tt * N + z;
+                            for_result<N>(cta, tt, [&](int idx, float re, float) {
                               Qo[idx] = re - __ldg(fi + idx) * V.LS[idx];
                             });
                           });
@@ -307,26 +340,16 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1) gemm_collision_kernel(
 
 // batched 3D DFT of complex volumes (XYZ passes, natural layout in and out)
 template <int N>
-__global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1)
+__global__ void __launch_bounds__(GemmGeo<N>::THREADS, GemmGeo<N>::MINB)
     dft3_batch_kernel(const float2* x, float2* y, int count, const uint16_t* mat, unsigned* status) {
   using G = GemmGeo<N>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_bbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int t = threadIdx.x;
   GemmCta<N> cta;
-  cta.A = reinterpret_cast<uint16_t*>(smem_raw);
-  cta.B = cta.A + G::A_ELEMS;
-  cta.bar = &s_bar;
-  cta.abort_flag = &s_abort;
-  cta.status = status;
-  cta.phase = 0;
-  if (t == 0) {
-    s_abort = 0;
-    tc::mbar_init(&s_bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  init_cta<N>(cta, smem_raw, &s_bar, s_bbar, &s_abort, status, t);
   for (int i = t; i < G::A_ELEMS / 8; i += G::THREADS) reinterpret_cast<uint4*>(cta.A)[i] = make_uint4(0, 0, 0, 0);
   if (t < 32) {
     tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
@@ -341,8 +364,8 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, 1)
     float2* dst = y + size_t(v) * G::N3;
     const bool ok = dft3<N, false>(cta, t, mat, mat, mat, [&](int tt) { src_cplx<N>(cta, tt, src, nullptr); },
                                    [&](int tt) {
-                                     for_result<N>(cta, tt, [&](int z, float re, float im) {
-                                       dst[tt * N + z] = make_float2(re, im);
+                                     for_result<N>(cta, tt, [&](int idx, float re, float im) {
+                                       dst[idx] = make_float2(re, im);
                                      });
                                    });
     if (!ok) break;

@@ -102,6 +102,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// ---- bulk copy (TMA, one-dimensional) ---------------------------------------------------
+// arm the barrier for `bytes` of asynchronous copies (one arrival by the calling thread)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to shared memory;
+// the barrier's transaction count drops by `bytes` when the data has landed
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // ---- TMEM loads and stores (32 lanes x 32 bits, 16 consecutive columns per thread) -------
 // warp w of the CTA reaches lanes 32 (w % 4) .. 32 (w % 4) + 31; taddr carries the lane in its
 // upper 16 bits and the column in its lower 16 bits

@@ -57,7 +57,7 @@ def flops_per_transform(N):
 
 # the sources that define the collision kernel's code and launch shape
 COLLISION_KERNEL_SOURCES = ("collision_kernel.cuh", "fft_line.cuh", "collision_f32.cu", "collision_f64.cu",
-                            "dgfs_internal.h", "tuned_shapes.h")
+                            "dgfs_internal.h", "tuned_shapes.h", "tuned_radix.h")
 
 
 def kernel_sources_sha1():
@@ -329,6 +329,7 @@ def serving_leg(args):
     stream = serve.mixed_stream(args.serve_requests, rate, seed=5001)
     st = eng.run(stream)
     out = st.as_dict()
+    out["fp64_comparison"] = fp64_serving_replay(ex, stream, st, chunk, args.serve_policy)
     out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
                 "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
                 "sm_share": args.serve_sm_share, "warmup_s": warm_s, "policy": args.serve_policy,
@@ -336,6 +337,42 @@ def serving_leg(args):
                 "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
                        "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
     return out
+
+
+def fp64_serving_replay(ex, stream, measured, chunk, policy):
+    """The plain FP64 path on the same request stream.  Serving the mix in FP64 for real takes
+    tens of minutes (one 4096-node N=48 three-species request alone is ~6 min of device time),
+    so the stream's arrival trace is replayed through the same chunk scheduler in virtual time
+    (serve.replay_chunked) with device service times measured per (N, s) for both precisions.
+    The FP32 replay is checked against the FP32 stream measured above; the FP64 replay is given
+    at the same arrivals (the FP64 path is then overloaded) and with the arrivals slowed to 75 %
+    of the FP64 path's own capacity."""
+    from paper_1903_03056_gb300 import serve
+    keys = sorted({(r.N, r.s) for r in stream})
+    spn32 = ex.service_seconds_per_node(keys, precision="fp32")
+    spn64 = ex.service_seconds_per_node(keys, precision="fp64")
+    chunk_s = chunk if chunk else 0.05
+    r32 = serve.replay_chunked(stream, lambda r: spn32[(r.N, r.s)], chunk_s, policy)
+    r64 = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy)
+    work32 = sum(r.batch * spn32[(r.N, r.s)] for r in stream)
+    work64 = sum(r.batch * spn64[(r.N, r.s)] for r in stream)
+    span = max(r.arrival for r in stream) - min(r.arrival for r in stream)
+    # arrivals stretched so that the FP64 path is 75 % busy over the stream
+    scale = (work64 / 0.75) / span if span > 0 else 1.0
+    r64s = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy, rate_scale=scale)
+
+    def brief(s):
+        return {"requests": s.n, "p50_ms": s.p50 * 1e3, "p99_ms": s.p99 * 1e3, "mean_ms": s.mean_latency * 1e3,
+                "makespan_s": s.makespan, "evals_per_s": s.evals_per_s}
+
+    return {"method": "trace replay of the measured stream's arrivals through the same SRPT chunk scheduler, "
+                      "device modelled as processor sharing, service times per (N, s) measured on this GPU",
+            "service_ms_per_node_fp32": {"%d,%d" % k: v * 1e3 for k, v in spn32.items()},
+            "service_ms_per_node_fp64": {"%d,%d" % k: v * 1e3 for k, v in spn64.items()},
+            "fp32_replay": brief(r32), "fp32_measured": {"p50_ms": measured.p50 * 1e3, "p99_ms": measured.p99 * 1e3},
+            "fp64_same_arrivals": brief(r64), "fp64_utilisation_at_same_arrivals": work64 / span if span > 0 else None,
+            "fp64_at_75pct_of_its_capacity": dict(brief(r64s), arrival_rate_per_s=len(stream) / (span * scale)),
+            "fp64_over_fp32_device_work": work64 / work32}
 
 
 def dg_leg(torch, w, stream, Ne=1024, K=4):
@@ -500,7 +537,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--serve-calib", type=int, default=24)
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-sm-share", type=float, default=1.0)
     ap.add_argument("--serve-chunk-s", type=float, default=0.05,
                     help="device seconds per chunk of a request (0: whole requests)")

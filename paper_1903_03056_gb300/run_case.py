@@ -17,6 +17,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--checksum", action="store_true", help="add the SHA-1 of the output bytes")
+    ap.add_argument("--compare-fp64", type=int, default=0, metavar="K",
+                    help="also evaluate the first K nodes with an FP64 plan and report the largest "
+                         "per-node max |Q - Q_fp64| / max |Q_fp64|")
     ap.add_argument("--n-rho", type=int, default=None,
                     help="override the workload's radial nodes (smaller tables for profiling)")
     a = ap.parse_args()
@@ -55,6 +58,15 @@ def main():
     if a.checksum:
         import hashlib
         out["sha1"] = hashlib.sha1(Q.cpu().numpy().tobytes()).hexdigest()
+    if a.compare_fp64 > 0:
+        K = min(a.compare_fp64, B)
+        p64 = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho, precision="fp64")
+        Q64 = p64.eval(fd[:K].double().contiguous())
+        torch.cuda.synchronize()
+        p64.close()
+        dims = tuple(range(1, Q64.dim()))
+        err = ((Q[:K].double() - Q64).abs().amax(dim=dims) / Q64.abs().amax(dim=dims)).max()
+        out["err_vs_fp64"] = float(err)
     print(json.dumps(out))
     plan.close()
 

@@ -313,6 +313,74 @@ class ServingEngine:
                      extra={"policy": self.policy, "chunk_s": self.chunk_s})
 
 
+def replay_chunked(requests, seconds_per_node, chunk_s, policy="srpt", slots=8, rate_scale=1.0):
+    """The chunked scheduler of ServingEngine._run_chunked replayed in virtual time: the same
+    arrivals (times multiplied by rate_scale), the same chunk sizes (cost model), the same
+    admission order and the same choice of the next chunk (srpt or fifo, one chunk per plan at
+    a time), with the device modelled as one server that works through the chunks in flight
+    side by side (processor sharing: k chunks in flight each advance at 1/k of the device).
+    seconds_per_node(r) is the measured device time per node of the request's (N, s) when it
+    has the whole device.  No memory budget (the replay is for a fixed mix that fits).
+    Returns Stats (latency = completion - arrival)."""
+    reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+    arr = [(r.arrival * rate_scale, r) for r in reqs]
+    left = {r.rid: r.batch for r in reqs}     # nodes not yet handed out
+    todo = {r.rid: r.batch for r in reqs}     # nodes not yet completed
+    done_at = {}
+    active = []                               # arrived requests with nodes to hand out
+    running = []                              # [remaining device seconds, request, nodes]
+    t, i = 0.0, 0
+    peak = 0
+
+    def pick():
+        busy = {r.plan_key for (_, r, _) in running}
+        cand = [r for r in active if left[r.rid] > 0 and r.plan_key not in busy]
+        if not cand:
+            return None
+        if policy == "fifo":
+            return min(cand, key=lambda r: (r.arrival, r.rid))
+        return min(cand, key=lambda r: (left[r.rid] * cost_per_node(r), r.arrival, r.rid))
+
+    while i < len(arr) or running or any(left[r.rid] > 0 for r in active):
+        while i < len(arr) and arr[i][0] <= t + 1e-15:
+            active.append(arr[i][1])
+            i += 1
+        while len(running) < slots:
+            r = pick()
+            if r is None:
+                break
+            n = min(left[r.rid], max(1, int(chunk_s / cost_per_node(r))))
+            left[r.rid] -= n
+            running.append([n * seconds_per_node(r), r, n])
+        peak = max(peak, len(running))
+        if not running:
+            if i < len(arr):
+                t = arr[i][0]
+                continue
+            break
+        k = len(running)
+        # next event: a chunk finishes (at rate 1/k) or a request arrives
+        dt_finish = min(c[0] for c in running) * k
+        dt_arrive = arr[i][0] - t if i < len(arr) else float("inf")
+        dt = min(dt_finish, dt_arrive)
+        for c in running:
+            c[0] -= dt / k
+        t += dt
+        for c in [c for c in running if c[0] <= 1e-12]:
+            running.remove(c)
+            r = c[1]
+            todo[r.rid] -= c[2]
+            if todo[r.rid] == 0:
+                done_at[r.rid] = t
+                active.remove(r)
+    lat = [done_at[r.rid] - r.arrival * rate_scale for r in reqs]
+    first = min(r.arrival for r in reqs) * rate_scale
+    return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=max(done_at.values()) - first,
+                 p50=percentile(lat, 50), p99=percentile(lat, 99), mean_latency=sum(lat) / len(lat),
+                 peak_bytes=0, peak_inflight=peak, budget=0,
+                 extra={"policy": policy, "chunk_s": chunk_s, "rate_scale": rate_scale})
+
+
 class FakeExecutor:
     """CPU model of the device for scheduler tests: a request occupies its slot for
     `seconds_per_node * batch` and needs a fixed number of bytes per node."""
@@ -496,6 +564,38 @@ class GpuExecutor:
                 self.release(r)
         torch.cuda.synchronize(self.dev)
         return time.perf_counter() - t0
+
+    # nodes per timed evaluation: enough work items to fill the device at every N
+    SERVICE_NODES = {8: 1024, 12: 1024, 16: 512, 24: 256, 32: 128, 48: 48}
+
+    def service_seconds_per_node(self, keys, precision=None):
+        """Device seconds per node with the whole device, per (N, s) in keys, measured with
+        CUDA events on one evaluation of SERVICE_NODES[N] nodes (after one warm-up evaluation)
+        with a plan of the serving mix's parameters (masses 1 .. 2.5, omega 0.75, M = 12,
+        N_rho = N/2) in `precision` (default: the executor's)."""
+        torch = self.torch
+        prec = precision or self.precision
+        dt = torch.float32 if prec != "fp64" else torch.float64
+        out = {}
+        for N, s in keys:
+            nodes = self.SERVICE_NODES[N]
+            masses = list(np.linspace(1.0, 2.5, s))
+            plan = self.dgfs.Plan(N, L_FOR_N[N], masses, 0.75, M=12, N_rho=N // 2, precision=prec)
+            pool = self._pool(N, s).to(dt)
+            idx = torch.arange(nodes, device=self.dev) % self.pool_nodes
+            f = pool.index_select(0, idx).contiguous()
+            Q = torch.empty((nodes, s, s, N, N, N), dtype=dt, device=self.dev)
+            st = torch.cuda.current_stream(self.dev)
+            plan.eval_ptr(f.data_ptr(), Q.data_ptr(), nodes, st)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            plan.eval_ptr(f.data_ptr(), Q.data_ptr(), nodes, st)
+            e1.record(st)
+            torch.cuda.synchronize(self.dev)
+            out[(N, s)] = e0.elapsed_time(e1) * 1e-3 / nodes
+            plan.close()
+            del f, Q
+        return out
 
     def run_alone(self, r):
         """Evaluate one request by itself (fresh plan, default stream); returns Q."""

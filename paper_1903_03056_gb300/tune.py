@@ -1,6 +1,7 @@
-"""Autotuner of the collision kernel's launch shape.
+"""Autotuner of the collision kernel's launch shape and of its line transforms' radix schedule.
 
     python -m paper_1903_03056_gb300.tune [--precision fp32] [--sizes 16 24 32 48] [--write]
+    python -m paper_1903_03056_gb300.tune --radix [--precision fp32] [--sizes 16 24 32 48] [--write]
 
 For every grid size N it builds the kernel once per candidate shape -- thread-block cluster
 size C, plane groups per CTA GP, CTAs per SM the registers are sized for (MB) -- in a
@@ -10,6 +11,13 @@ checks that its output is bitwise identical to the current build's (a shape chan
 thread computes a line, never the arithmetic of a line), and keeps the fastest.  With
 --write the winners replace their lines of csrc/tuned_shapes.h and every timing is recorded
 in csrc/tuned_shapes.json; rebuild afterwards.
+
+With --radix it times, per N, every order of the radices 8, 4, 2, 3 in the candidate list
+(tuned_radix.h codes) of the FP32 kernel instead.  A schedule changes the rounding of a line,
+so its output is checked against the FP64 path on the first nodes of the workload (the largest
+per-node max |Q - Q_fp64| / max |Q_fp64| must stay below the FP32 bar, 1e-5); the fastest
+schedule that passes is kept.  (FP64 schedules stay at the default order: an FP64 variant has
+no more accurate path to be checked against on the device.)
 """
 
 import argparse
@@ -40,6 +48,39 @@ CANDIDATES = {
          (2, 2, 6)],
     48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2), (4, 4, 1), (4, 2, 1), (8, 2, 1)],
 }
+
+
+RADIX_H = os.path.join(CSRC, "tuned_radix.h")
+# orders of the radix multisets of each N (4-stage and longer schedules left out)
+RADIX_CANDIDATES = {
+    12: [43, 34, 223, 232, 322],
+    16: [44, 82, 28, 422, 242, 224],
+    24: [423, 83, 38, 432, 243, 342, 234, 324],
+    32: [442, 84, 48, 424, 244, 822, 282, 228],
+    48: [443, 434, 344, 823, 832, 283, 238, 382, 328],
+}
+RADIX_BAR = 1e-5
+RADIX_CHECK_NODES = 4
+
+
+def radix_code_valid(N, code):
+    """A schedule's radices are 2, 3, 4 or 8 and multiply to N."""
+    digits = [int(c) for c in str(code)]
+    prod = 1
+    for d in digits:
+        prod *= d
+    return all(d in (2, 3, 4, 8) for d in digits) and prod == N
+
+
+def _radix_line(T, N, code):
+    return "DGFS_RADIX(%s, %d, %d)" % (T, N, code)
+
+
+def _patch_radix(text, T, N, line):
+    pat = re.compile(r"^DGFS_RADIX\(%s, %d, \d+\)$" % (T, N), re.M)
+    if not pat.search(text):
+        raise RuntimeError("no radix line for %s N=%d" % (T, N))
+    return pat.sub(line, text)
 
 
 def geometry(N, C, GP, MB, csize):
@@ -84,11 +125,12 @@ def _patch(text, T, N, line):
     return pat.sub(line, text)
 
 
-def _variant(tmp, precision, N, shape):
-    """Build a variant tree under tmp; returns its root (with the package inside)."""
+def _variant(tmp, precision, N, shape, radix=None):
+    """Build a variant tree under tmp; returns its root (with the package inside).  With
+    `radix` the shape stays and the radix schedule of (precision, N) becomes `radix`."""
     T = _ctype(precision)
     C, GP, MB = shape
-    root = os.path.join(tmp, "%s_%d_%d_%d_%d" % (precision, N, C, GP, MB))
+    root = os.path.join(tmp, "%s_%d_%d_%d_%d_r%s" % (precision, N, C, GP, MB, radix))
     pkg = os.path.join(root, "paper_1903_03056_gb300")
     os.makedirs(os.path.join(pkg, "_build"))
     for f in os.listdir(PKG):
@@ -101,6 +143,12 @@ def _variant(tmp, precision, N, shape):
         text = fh.read()
     with open(h, "w") as fh:
         fh.write(_patch(text, T, N, _shape_line(T, N, C, GP, MB)))
+    if radix is not None:
+        rh = os.path.join(pkg, "csrc", "tuned_radix.h")
+        with open(rh) as fh:
+            text = fh.read()
+        with open(rh, "w") as fh:
+            fh.write(_patch_radix(text, T, N, _radix_line(T, N, radix)))
     tu = "collision_f32" if precision == "fp32" else "collision_f64"
     obj = os.path.join(pkg, "_build", tu + ".o")
     cmd = ([build.nvcc()] + build.ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -119,10 +167,11 @@ def _variant(tmp, precision, N, shape):
     return root
 
 
-def _time(root, workload, batch, precision):
+def _time(root, workload, batch, precision, compare=0):
     env = dict(os.environ, PYTHONPATH=root + os.pathsep + ROOT)
+    extra = ["--compare-fp64", str(compare)] if compare else []
     res = subprocess.run([sys.executable, "-m", "paper_1903_03056_gb300.run_case", "--workload", workload,
-                          "--batch", str(batch), "--precision", precision, "--repeat", "3", "--checksum"],
+                          "--batch", str(batch), "--precision", precision, "--repeat", "3", "--checksum"] + extra,
                          capture_output=True, text=True, cwd=root, env=env)
     if res.returncode != 0:
         raise RuntimeError(res.stderr[-2000:])
@@ -170,12 +219,77 @@ def tune(precision="fp32", sizes=(16, 24, 32, 48), write=False, jobs=8):
     return record
 
 
+def current_shape(precision, N):
+    """(cluster, groups, CTAs per SM) of (precision, N) in tuned_shapes.h."""
+    T = _ctype(precision)
+    with open(SHAPES_H) as fh:
+        text = fh.read()
+    m = re.search(r"^DGFS_SHAPE(3?)\(%s, %d, (\d+), (\d+)(?:, (\d+))?\)$" % (T, N), text, re.M)
+    return int(m.group(2)), int(m.group(3)), int(m.group(4) or 1)
+
+
+def current_radix(precision, N):
+    with open(RADIX_H) as fh:
+        m = re.search(r"^DGFS_RADIX\(%s, %d, (\d+)\)$" % (_ctype(precision), N), fh.read(), re.M)
+    return int(m.group(1))
+
+
+def tune_radix(precision="fp32", sizes=(16, 24, 32, 48), write=False, jobs=8):
+    """Time every candidate radix schedule of each N at the current launch shape; keep the fastest
+    whose output stays within RADIX_BAR of the FP64 path."""
+    if precision != "fp32":
+        raise ValueError("radix schedules are tuned for the FP32 kernel")
+    build.build()
+    T = _ctype(precision)
+    record = {}
+    if os.path.exists(SHAPES_JSON):
+        with open(SHAPES_JSON) as fh:
+            record = json.load(fh)
+    with open(RADIX_H) as fh:
+        header = fh.read()
+    with tempfile.TemporaryDirectory(prefix="dgfs_tune_") as tmp:
+        todo = [(N, code) for N in sizes for code in RADIX_CANDIDATES.get(N, []) if radix_code_valid(N, code)]
+        with ThreadPoolExecutor(max_workers=jobs) as ex:
+            roots = dict(zip(todo, ex.map(lambda t: _variant(tmp, precision, t[0], current_shape(precision, t[0]),
+                                                             radix=t[1]), todo)))
+        for N in sizes:
+            workload, batch = WORKLOAD_FOR_N[N]
+            cur = current_radix(precision, N)
+            rows = []
+            for code in RADIX_CANDIDATES.get(N, []):
+                if (N, code) not in roots:
+                    continue
+                r = _time(roots[(N, code)], workload, batch, precision, compare=RADIX_CHECK_NODES)
+                ok = r["err_vs_fp64"] < RADIX_BAR
+                rows.append({"radix": code, "ms": r["ms"], "err_vs_fp64": r["err_vs_fp64"], "ok": ok})
+                print("%s N=%d radix %d: %.2f ms, error vs FP64 %.2e%s" % (precision, N, code, r["ms"], r["err_vs_fp64"],
+                      "" if ok else "  (above the bar: rejected)"), flush=True)
+            good = [r for r in rows if r["ok"]]
+            if not good:
+                continue
+            best = min(good, key=lambda r: r["ms"])
+            record["radix/%s/%d" % (precision, N)] = {"workload": workload, "batch": batch, "previous": cur,
+                                                     "shape": list(current_shape(precision, N)), "best": best,
+                                                     "candidates": rows}
+            header = _patch_radix(header, T, N, _radix_line(T, N, best["radix"]))
+    if write:
+        with open(RADIX_H, "w") as fh:
+            fh.write(header)
+        with open(SHAPES_JSON, "w") as fh:
+            json.dump(record, fh, indent=1, sort_keys=True)
+    return record
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--sizes", type=int, nargs="+", default=[16, 24, 32, 48])
     ap.add_argument("--write", action="store_true")
     ap.add_argument("--jobs", type=int, default=8)
+    ap.add_argument("--radix", action="store_true", help="tune the radix schedules instead of the launch shapes")
     a = ap.parse_args()
-    rec = tune(a.precision, tuple(a.sizes), a.write, a.jobs)
+    if a.radix:
+        rec = tune_radix(a.precision, tuple(a.sizes), a.write, a.jobs)
+    else:
+        rec = tune(a.precision, tuple(a.sizes), a.write, a.jobs)
     print(json.dumps({k: v["best"] for k, v in rec.items()}, indent=1))

@@ -109,3 +109,40 @@ def test_chunked_mode_runs_one_chunk_per_plan_at_a_time():
     eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=4, chunk_s=0.0005, policy="srpt")
     eng.run(reqs)
     assert fake.max_active == 1   # all three share one plan key
+
+
+# ---- replay of a stream in virtual time (the FP64 comparison of the serving report) --------
+
+def _req(rid, arrival, N, batch, s=2):
+    return serve.Request(rid, arrival, N, serve.L_FOR_N[N], tuple([1.0] * s), 0.75, 12, N // 2, batch)
+
+
+def test_replay_single_request_takes_its_service_time():
+    r = _req(0, 0.5, 16, 300)
+    st = serve.replay_chunked([r], lambda q: 1e-4, chunk_s=0.05)
+    assert abs(st.p50 - 300 * 1e-4) < 1e-9 and abs(st.makespan - 300 * 1e-4) < 1e-9
+
+
+def test_replay_conserves_work_and_lets_small_requests_overtake():
+    """All requests at t = 0 on an idle device: the makespan is the total work (the device never
+    idles), and under SRPT the one-node request finishes long before the large one."""
+    reqs = [_req(0, 0.0, 32, 4000), _req(1, 0.0, 32, 1), _req(2, 0.0, 16, 50)]
+    spn = {32: 1e-4, 16: 1e-5}
+    st = serve.replay_chunked(reqs, lambda q: spn[q.N], chunk_s=0.05)
+    work = 4000 * 1e-4 + 1e-4 + 50 * 1e-5
+    assert abs(st.makespan - work) < 1e-9
+    st_f = serve.replay_chunked(reqs, lambda q: spn[q.N], chunk_s=0.05, policy="fifo")
+    assert abs(st_f.makespan - work) < 1e-9
+    # the small requests' latencies: SRPT far below FIFO
+    assert st.p50 < 0.05 * st_f.p50
+
+
+def test_replay_latency_grows_with_the_service_time_and_the_arrival_scale():
+    reqs = serve.mixed_stream(40, 20.0, seed=77)
+    fast = serve.replay_chunked(reqs, lambda q: 1e-5, chunk_s=0.05)
+    slow = serve.replay_chunked(reqs, lambda q: 3e-4, chunk_s=0.05)
+    assert slow.p50 > fast.p50 and slow.p99 > fast.p99
+    # stretching the arrivals by the slowdown relieves the queue
+    relaxed = serve.replay_chunked(reqs, lambda q: 3e-4, chunk_s=0.05, rate_scale=30.0)
+    assert relaxed.p99 < slow.p99
+    assert relaxed.n == slow.n == 40 and relaxed.nodes == sum(r.batch for r in reqs)

@@ -47,3 +47,25 @@ def test_shape_line_round_trip():
     text = open(tune.SHAPES_H).read()
     assert tune._patch(text, "float", 32, line).count(line) == 1
     assert os.path.exists(tune.SHAPES_JSON)
+
+
+def _committed_radix():
+    text = open(tune.RADIX_H).read()
+    return [(m.group(1), int(m.group(2)), int(m.group(3)))
+            for m in re.finditer(r"^DGFS_RADIX\((float|double), (\d+), (\d+)\)$", text, re.M)]
+
+
+def test_every_supported_size_has_a_valid_radix_schedule_per_precision():
+    rows = _committed_radix()
+    for T in ("float", "double"):
+        assert sorted(N for t, N, _ in rows if t == T) == [4, 6, 8, 12, 16, 24, 32, 48]
+    for T, N, code in rows:
+        assert tune.radix_code_valid(N, code), (T, N, code)
+
+
+def test_radix_candidates_are_orders_of_valid_schedules():
+    for N, codes in tune.RADIX_CANDIDATES.items():
+        assert len(set(codes)) == len(codes)
+        for code in codes:
+            assert tune.radix_code_valid(N, code), (N, code)
+        assert not tune.radix_code_valid(N, codes[0] * 10 + 2)

@@ -314,9 +314,10 @@ def time_steps(torch, fn, steps, warmup, stream, dist=None):
 def serving_leg(args):
     """The mixed request stream: N in {16, 24, 32, 48}, s in {2, 3}, masses U[1, 4], VHS
     omega U[0.5, 1], batches of 1..4096 nodes, FP32, 120 GB HBM budget, 8 slots, requests
-    served in chunks of ~50 ms of device work, shortest remaining work first.  A closed-loop
-    run of the first requests measures the mix's throughput; the Poisson stream then arrives
-    at 75% of it."""
+    served in chunks of ~50 ms of device work, shortest remaining work first.  The device
+    time per node of every (N, s) is measured first; the Poisson arrivals are then scaled so
+    that the stream's device work keeps the GPU 75 % busy over the stream.  A closed-loop run
+    of the first requests reports the engine's capacity on the mix."""
     from paper_1903_03056_gb300 import serve
     budget = 120 << 30
     ex = serve.GpuExecutor(slots=8, sm_share=args.serve_sm_share)
@@ -325,21 +326,28 @@ def serving_leg(args):
     eng = serve.ServingEngine(ex, budget_bytes=budget, slots=8, chunk_s=chunk, policy=args.serve_policy)
     calib = serve.mixed_stream(args.serve_calib, math.inf, seed=5000)
     st0 = eng.run(calib)
-    rate = 0.75 * st0.n / st0.makespan
-    stream = serve.mixed_stream(args.serve_requests, rate, seed=5001)
+    stream = serve.mixed_stream(args.serve_requests, 1.0, seed=5001)
+    keys = sorted({(r.N, r.s) for r in stream})
+    spn32 = ex.service_seconds_per_node(keys, precision="fp32")
+    work = sum(r.batch * spn32[(r.N, r.s)] for r in stream)
+    span = max(r.arrival for r in stream)
+    scale = (work / 0.75) / span
+    for r in stream:
+        r.arrival *= scale
+    rate = len(stream) / (span * scale)
     st = eng.run(stream)
     out = st.as_dict()
-    out["fp64_comparison"] = fp64_serving_replay(ex, stream, st, chunk, args.serve_policy)
-    out.update({"arrival_rate_per_s": rate, "closed_loop_requests": st0.n,
-                "closed_loop_evals_per_s": st0.evals_per_s, "closed_loop_req_per_s": st0.n / st0.makespan,
-                "sm_share": args.serve_sm_share, "warmup_s": warm_s, "policy": args.serve_policy,
-                "chunk_s": chunk,
+    out["fp64_comparison"] = fp64_serving_replay(ex, stream, st, chunk, args.serve_policy, spn32, budget)
+    out.update({"arrival_rate_per_s": rate, "target_utilisation": 0.75, "stream_device_work_s": work,
+                "closed_loop_requests": st0.n, "closed_loop_evals_per_s": st0.evals_per_s,
+                "closed_loop_req_per_s": st0.n / st0.makespan, "sm_share": args.serve_sm_share,
+                "warmup_s": warm_s, "policy": args.serve_policy, "chunk_s": chunk,
                 "mix": "N in {16,24,32,48}, s in {2,3}, masses U[1,4], omega U[0.5,1], batch "
                        "round(exp U[0, ln 4096]), M=12, N_rho=N/2, FP32, 8 slots, 120 GB budget"})
     return out
 
 
-def fp64_serving_replay(ex, stream, measured, chunk, policy):
+def fp64_serving_replay(ex, stream, measured, chunk, policy, spn32, budget):
     """The plain FP64 path on the same request stream.  Serving the mix in FP64 for real takes
     tens of minutes (one 4096-node N=48 three-species request alone is ~6 min of device time),
     so the stream's arrival trace is replayed through the same chunk scheduler in virtual time
@@ -349,24 +357,27 @@ def fp64_serving_replay(ex, stream, measured, chunk, policy):
     of the FP64 path's own capacity."""
     from paper_1903_03056_gb300 import serve
     keys = sorted({(r.N, r.s) for r in stream})
-    spn32 = ex.service_seconds_per_node(keys, precision="fp32")
     spn64 = ex.service_seconds_per_node(keys, precision="fp64")
     chunk_s = chunk if chunk else 0.05
-    r32 = serve.replay_chunked(stream, lambda r: spn32[(r.N, r.s)], chunk_s, policy)
-    r64 = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy)
+    b32 = lambda r: serve.request_bytes(r, 4)  # noqa: E731
+    b64 = lambda r: serve.request_bytes(r, 8)  # noqa: E731
+    r32 = serve.replay_chunked(stream, lambda r: spn32[(r.N, r.s)], chunk_s, policy, bytes_of=b32, budget=budget)
+    r64 = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy, bytes_of=b64, budget=budget)
     work32 = sum(r.batch * spn32[(r.N, r.s)] for r in stream)
     work64 = sum(r.batch * spn64[(r.N, r.s)] for r in stream)
     span = max(r.arrival for r in stream) - min(r.arrival for r in stream)
     # arrivals stretched so that the FP64 path is 75 % busy over the stream
     scale = (work64 / 0.75) / span if span > 0 else 1.0
-    r64s = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy, rate_scale=scale)
+    r64s = serve.replay_chunked(stream, lambda r: spn64[(r.N, r.s)], chunk_s, policy, rate_scale=scale,
+                                bytes_of=b64, budget=budget)
 
     def brief(s):
         return {"requests": s.n, "p50_ms": s.p50 * 1e3, "p99_ms": s.p99 * 1e3, "mean_ms": s.mean_latency * 1e3,
                 "makespan_s": s.makespan, "evals_per_s": s.evals_per_s}
 
-    return {"method": "trace replay of the measured stream's arrivals through the same SRPT chunk scheduler, "
-                      "device modelled as processor sharing, service times per (N, s) measured on this GPU",
+    return {"method": "trace replay of the measured stream's arrivals through the same SRPT chunk scheduler and "
+                      "HBM-budget admission, device modelled as processor sharing, service times per (N, s) "
+                      "measured on this GPU (plan building not modelled)",
             "service_ms_per_node_fp32": {"%d,%d" % k: v * 1e3 for k, v in spn32.items()},
             "service_ms_per_node_fp64": {"%d,%d" % k: v * 1e3 for k, v in spn64.items()},
             "fp32_replay": brief(r32), "fp32_measured": {"p50_ms": measured.p50 * 1e3, "p99_ms": measured.p99 * 1e3},

@@ -105,6 +105,12 @@ def cost_per_node(r):
     return COST_PER_TRANSFORM_POINT * r.s * r.s * r.N_rho * r.M * n3 * math.log2(n3)
 
 
+def request_bytes(r, elem=4, plan_bytes=0):
+    """Device bytes a request holds while admitted: its input f [batch][s][N^3] and output Q
+    [batch][s][s][N^3] in the precision's element size, plus its plan."""
+    return plan_bytes + r.batch * (r.s + r.s * r.s) * r.N ** 3 * elem
+
+
 def percentile(values, p):
     v = sorted(values)
     if not v:
@@ -313,24 +319,28 @@ class ServingEngine:
                      extra={"policy": self.policy, "chunk_s": self.chunk_s})
 
 
-def replay_chunked(requests, seconds_per_node, chunk_s, policy="srpt", slots=8, rate_scale=1.0):
+def replay_chunked(requests, seconds_per_node, chunk_s, policy="srpt", slots=8, rate_scale=1.0,
+                   bytes_of=None, budget=None):
     """The chunked scheduler of ServingEngine._run_chunked replayed in virtual time: the same
     arrivals (times multiplied by rate_scale), the same chunk sizes (cost model), the same
-    admission order and the same choice of the next chunk (srpt or fifo, one chunk per plan at
-    a time), with the device modelled as one server that works through the chunks in flight
-    side by side (processor sharing: k chunks in flight each advance at 1/k of the device).
+    admission in arrival order under the memory budget (when bytes_of and budget are given)
+    and the same choice of the next chunk (srpt or fifo, one chunk per plan at a time), with
+    the device modelled as one server that works through the chunks in flight side by side
+    (processor sharing: k chunks in flight each advance at 1/k of the device).
     seconds_per_node(r) is the measured device time per node of the request's (N, s) when it
-    has the whole device.  No memory budget (the replay is for a fixed mix that fits).
-    Returns Stats (latency = completion - arrival)."""
+    has the whole device.  Plan building is not modelled.  Returns Stats (latency =
+    completion - arrival)."""
     reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
     arr = [(r.arrival * rate_scale, r) for r in reqs]
     left = {r.rid: r.batch for r in reqs}     # nodes not yet handed out
     todo = {r.rid: r.batch for r in reqs}     # nodes not yet completed
     done_at = {}
-    active = []                               # arrived requests with nodes to hand out
+    waiting = collections.deque()             # arrived, not yet admitted (arrival order)
+    active = []                               # admitted requests with nodes to hand out
     running = []                              # [remaining device seconds, request, nodes]
     t, i = 0.0, 0
     peak = 0
+    in_use, peak_bytes = 0, 0
 
     def pick():
         busy = {r.plan_key for (_, r, _) in running}
@@ -341,10 +351,18 @@ def replay_chunked(requests, seconds_per_node, chunk_s, policy="srpt", slots=8, 
             return min(cand, key=lambda r: (r.arrival, r.rid))
         return min(cand, key=lambda r: (left[r.rid] * cost_per_node(r), r.arrival, r.rid))
 
-    while i < len(arr) or running or any(left[r.rid] > 0 for r in active):
+    while i < len(arr) or running or waiting or any(left[r.rid] > 0 for r in active):
         while i < len(arr) and arr[i][0] <= t + 1e-15:
-            active.append(arr[i][1])
+            waiting.append(arr[i][1])
             i += 1
+        while waiting:
+            need = bytes_of(waiting[0]) if bytes_of else 0
+            if budget is not None and in_use + need > budget and (active or running):
+                break
+            r = waiting.popleft()
+            in_use += need
+            peak_bytes = max(peak_bytes, in_use)
+            active.append(r)
         while len(running) < slots:
             r = pick()
             if r is None:
@@ -373,11 +391,12 @@ def replay_chunked(requests, seconds_per_node, chunk_s, policy="srpt", slots=8, 
             if todo[r.rid] == 0:
                 done_at[r.rid] = t
                 active.remove(r)
+                in_use -= bytes_of(r) if bytes_of else 0
     lat = [done_at[r.rid] - r.arrival * rate_scale for r in reqs]
     first = min(r.arrival for r in reqs) * rate_scale
     return Stats(n=len(reqs), nodes=sum(r.batch for r in reqs), makespan=max(done_at.values()) - first,
                  p50=percentile(lat, 50), p99=percentile(lat, 99), mean_latency=sum(lat) / len(lat),
-                 peak_bytes=0, peak_inflight=peak, budget=0,
+                 peak_bytes=peak_bytes, peak_inflight=peak, budget=budget or 0,
                  extra={"policy": policy, "chunk_s": chunk_s, "rate_scale": rate_scale})
 
 

@@ -146,3 +146,19 @@ def test_replay_latency_grows_with_the_service_time_and_the_arrival_scale():
     relaxed = serve.replay_chunked(reqs, lambda q: 3e-4, chunk_s=0.05, rate_scale=30.0)
     assert relaxed.p99 < slow.p99
     assert relaxed.n == slow.n == 40 and relaxed.nodes == sum(r.batch for r in reqs)
+
+
+def test_replay_admits_in_arrival_order_under_the_budget():
+    """Two requests that do not fit the budget together: the second is admitted only when the
+    first completes, so its latency includes the first's service time."""
+    a, b = _req(0, 0.0, 32, 100), _req(1, 0.0, 32, 100)
+    spn = lambda q: 1e-3  # noqa: E731
+    one = serve.request_bytes(a)
+    st = serve.replay_chunked([a, b], spn, chunk_s=0.05, bytes_of=serve.request_bytes, budget=int(1.5 * one))
+    assert abs(st.makespan - 0.2) < 1e-9 and st.peak_bytes == one
+    both = serve.replay_chunked([a, b], spn, chunk_s=0.05, bytes_of=serve.request_bytes, budget=3 * one)
+    assert both.peak_bytes == 2 * one
+    # serialised by the budget: latencies 0.1 s and 0.2 s (median 0.15 s); sharing the device,
+    # both finish at 0.2 s
+    assert abs(st.p50 - 0.15) < 1e-9
+    assert abs(both.p50 - 0.2) < 1e-9

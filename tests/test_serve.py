@@ -151,7 +151,8 @@ def test_replay_latency_grows_with_the_service_time_and_the_arrival_scale():
 def test_replay_admits_in_arrival_order_under_the_budget():
     """Two requests that do not fit the budget together: the second is admitted only when the
     first completes, so its latency includes the first's service time."""
-    a, b = _req(0, 0.0, 32, 100), _req(1, 0.0, 32, 100)
+    a = _req(0, 0.0, 32, 100)
+    b = serve.Request(1, 0.0, 32, serve.L_FOR_N[32], (1.0, 1.5), 0.75, 12, 16, 100)  # another plan
     spn = lambda q: 1e-3  # noqa: E731
     one = serve.request_bytes(a)
     st = serve.replay_chunked([a, b], spn, chunk_s=0.05, bytes_of=serve.request_bytes, budget=int(1.5 * one))

@@ -109,6 +109,7 @@ struct Plan {
   int n_fslot = 0;              // slots per (pair, rho) of the VSS table
   int n_t = 64;                 // points of the VSS gain weight's Gauss-Jacobi rule in t
   double vss_a_max = 0;         // largest argument pi rho c_j |k| / L of that table
+  bool vss_grid = false;        // the table was built from the grid of Phi_alpha(p, q)
   bool antipodal = false;       // every direction has an antipode of equal weight
   std::vector<int> ent_ysh;     // [entries] shares the previous entry's y pass
   int max_ent = 0;
@@ -191,6 +192,16 @@ int launch_gain_tables_f32(Plan& p, int self_sum);
 int launch_to_f32(const Plan& p, const double* src, float* dst, size_t n);
 int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_t, const double* d_sigma,
                       const int* d_reps, int n_reps);
+// the grid of Phi_alpha(p, q) behind the fast build of a VSS table (FP32 plans)
+struct VssGrid {
+  int np = 0, nq = 0;
+  double p0 = 0, q0 = 0, h = 0;
+};
+// Phi grids of the distinct alpha (rules d_gj [n_alpha][3][n_t]) into d_phi [n_alpha][nq][np],
+// then the gain table by interpolation (pair o reads grid d_grid_of_pair[o])
+int launch_vss_tables_grid(Plan& p, const double* d_fcoef, double2* d_phi, const double* d_gj, int n_alpha, int n_t,
+                           const VssGrid& gr, const int* d_grid_of_pair, const double* d_sigma, const int* d_reps,
+                           int n_reps);
 
 // split-BF16 tensor-core path (dft_gemm.cu): N it supports, matrix images from the plan's
 // phase factors [task][rho][max_ent][role][axis][N], kernel configuration and launch

@@ -638,9 +638,53 @@ int upload_plan(Plan& p) {
     if ((rc = up_tmp(gj.data(), gj.size(), &d_gj))) return rc;
     if ((rc = up_tmp(p.sigma.data(), p.sigma.size(), &d_sg))) return rc;
     if ((rc = up_tmp(reps.data(), reps.size(), &d_reps))) return rc;
-    if ((rc = launch_vss_tables(p, static_cast<double*>(d_vc), static_cast<double*>(d_gj), n_t,
-                                static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size()))))
+    // FP32 plans build the table from a grid of the two-argument function Phi_alpha(p, q) (one
+    // grid per distinct alpha, spacing 0.03: 4 x 4-point interpolation within 3e-9 of the
+    // integral's bound at arguments up to 65); FP64 plans, and grids that would be too large,
+    // sum the Gauss-Jacobi rule for every entry
+    VssGrid gr;
+    gr.h = 0.03;
+    const double A = p.vss_a_max;
+    std::vector<double> alphas;
+    std::vector<int> grid_of_pair(P);
+    for (int o = 0; o < P; ++o) {
+      int g = -1;
+      for (size_t a = 0; a < alphas.size(); ++a)
+        if (alphas[a] == p.alpha[o]) g = int(a);
+      if (g < 0) {
+        g = int(alphas.size());
+        alphas.push_back(p.alpha[o]);
+      }
+      grid_of_pair[o] = g;
+    }
+    gr.p0 = -A - 2.0 * gr.h;
+    gr.q0 = -2.0 * gr.h;
+    gr.np = int(std::ceil((2.0 * A + 4.0 * gr.h) / gr.h)) + 2;
+    gr.nq = int(std::ceil((A + 4.0 * gr.h) / gr.h)) + 2;
+    const size_t grid_bytes = alphas.size() * size_t(gr.np) * gr.nq * sizeof(double2);
+    const size_t direct_terms = size_t(P) * NR * reps.size() * N3;
+    p.vss_grid = p.f32io() && grid_bytes <= (size_t(1) << 30) && size_t(gr.np) * gr.nq < direct_terms;
+    if (p.vss_grid) {
+      std::vector<double> gja(alphas.size() * 3 * n_t);
+      for (size_t a = 0; a < alphas.size(); ++a) {
+        int o = 0;
+        while (grid_of_pair[o] != int(a)) ++o;
+        std::copy(gj.begin() + size_t(o) * 3 * n_t, gj.begin() + size_t(o + 1) * 3 * n_t, gja.begin() + a * 3 * n_t);
+      }
+      void *d_phi = nullptr, *d_gja = nullptr, *d_gop = nullptr;
+      if ((rc = dalloc(p, &d_phi, grid_bytes))) return rc;
+      temps.v.push_back(d_phi);
+      if ((rc = up_tmp(gja.data(), gja.size(), &d_gja))) return rc;
+      if ((rc = up_tmp(grid_of_pair.data(), grid_of_pair.size(), &d_gop))) return rc;
+      if ((rc = launch_vss_tables_grid(p, static_cast<double*>(d_vc), static_cast<double2*>(d_phi),
+                                       static_cast<double*>(d_gja), int(alphas.size()), n_t, gr,
+                                       static_cast<int*>(d_gop), static_cast<double*>(d_sg),
+                                       static_cast<int*>(d_reps), int(reps.size()))))
+        return rc;
+    } else if ((rc = launch_vss_tables(p, static_cast<double*>(d_vc), static_cast<double*>(d_gj), n_t,
+                                       static_cast<double*>(d_sg), static_cast<int*>(d_reps), int(reps.size())))) {
       return rc;
+    }
     if ((rc = launch_loss_table(p, static_cast<double*>(d_gcoef), static_cast<double*>(d_gscale), NL))) return rc;
     if ((rc = upload(p, p.ent_m.data(), p.ent_m.size(), (void**)&p.d_ent_m, total))) return rc;
   }

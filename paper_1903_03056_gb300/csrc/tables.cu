@@ -76,6 +76,81 @@ __global__ void vss_table_kernel(double2* __restrict__ Fv, int P, int NR, int N,
   }
 }
 
+// The VSS gain weight depends on (k, rho, sigma) only through two numbers (Sec. 4, F after
+// Eq. GG): F = pref(rho) Phi_alpha(p, q) with p = s k.sigma, q = s |k x sigma|, s = pi rho c_j / L,
+// and Phi_alpha(p, q) = int_{-1}^{1} (1+t)^(alpha-1) exp(-i t p) J0(sqrt(1-t^2) q) dt.
+// phi_grid_kernel tabulates Phi on a uniform grid p = p0 + i h, q = q0 + j h (q0 = -2h: J0 is
+// even, so the rows below q = 0 mirror the ones above); vss_from_phi_kernel fills the gain table
+// by 4 x 4-point Lagrange interpolation on that grid, in FP64.
+__global__ void phi_grid_kernel(double2* __restrict__ phi, int np, int nq, double p0, double q0, double h,
+                                const double* __restrict__ gj, int n_t) {
+  const size_t count = size_t(np) * nq;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < count; idx += size_t(gridDim.x) * blockDim.x) {
+    const double p = p0 + double(idx % np) * h, q = q0 + double(idx / np) * h;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < n_t; ++k) {
+      double sv, cv;
+      sincos(gj[k] * p, &sv, &cv);
+      const double j = gj[n_t + k] * j0(gj[2 * n_t + k] * q);
+      re += cv * j;
+      im -= sv * j;
+    }
+    phi[idx] = make_double2(re, im);
+  }
+}
+
+// cubic Lagrange weights of the stencil points -1, 0, 1, 2 at the fraction f in [0, 1)
+__device__ __forceinline__ void lagrange4(double f, double (&w)[4]) {
+  w[0] = -f * (f - 1.0) * (f - 2.0) / 6.0;
+  w[1] = (f + 1.0) * (f - 1.0) * (f - 2.0) / 2.0;
+  w[2] = -(f + 1.0) * f * (f - 2.0) / 2.0;
+  w[3] = (f + 1.0) * f * (f - 1.0) / 6.0;
+}
+
+__global__ void vss_from_phi_kernel(double2* __restrict__ Fv, int P, int NR, int N, const double* __restrict__ coef,
+                                    const double2* __restrict__ phi, const int* __restrict__ grid_of_pair, int np,
+                                    int nq, double p0, double q0, double h, const double* __restrict__ sigma,
+                                    const int* __restrict__ reps, int n_reps) {
+  const size_t N3 = size_t(N) * N * N;
+  const size_t count = size_t(P) * NR * n_reps * N3;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < count; idx += size_t(gridDim.x) * blockDim.x) {
+    const size_t n = idx % N3;
+    const int r = int((idx / N3) % n_reps);
+    const size_t oq = idx / (N3 * n_reps);  // o * NR + q
+    const int o = int(oq / NR);
+    const int m = reps[r];
+    const int a_ = int(n / (size_t(N) * N)), b_ = int((n / N) % N), c_ = int(n % N);
+    const double kx = a_ < N / 2 ? a_ : a_ - N, ky = b_ < N / 2 ? b_ : b_ - N, kz = c_ < N / 2 ? c_ : c_ - N;
+    const double s = coef[2 * oq + 1];
+    const double kd = kx * sigma[3 * m] + ky * sigma[3 * m + 1] + kz * sigma[3 * m + 2];
+    const double pv = s * kd;
+    const double qv = s * sqrt(fmax(0.0, kx * kx + ky * ky + kz * kz - kd * kd));
+    const double u = (pv - p0) / h, v = (qv - q0) / h;
+    int iu = int(floor(u)), iv = int(floor(v));
+    iu = iu < 1 ? 1 : (iu > np - 3 ? np - 3 : iu);
+    iv = iv < 1 ? 1 : (iv > nq - 3 ? nq - 3 : iv);
+    double wu[4], wv[4];
+    lagrange4(u - iu, wu);
+    lagrange4(v - iv, wv);
+    const double2* g = phi + size_t(grid_of_pair[o]) * np * nq;
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double rr = 0.0, ii = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double2 z = g[size_t(iv - 1 + b) * np + (iu - 1 + a)];
+        rr += wu[a] * z.x;
+        ii += wu[a] * z.y;
+      }
+      re += wv[b] * rr;
+      im += wv[b] * ii;
+    }
+    const double pref = coef[2 * oq];
+    Fv[(oq * n_reps + r) * N3 + n] = make_double2(pref * re, pref * im);
+  }
+}
+
 __global__ void gain_to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
     dst[i] = float(src[i]);
@@ -129,6 +204,23 @@ int launch_vss_tables(Plan& p, const double* d_fcoef, const double* d_gj, int n_
   const unsigned blocks = unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536);
   vss_table_kernel<<<blocks, 256, 0, p.home>>>(p.d_Fv, p.s * p.s, p.N_rho, p.N, d_fcoef, d_gj, n_t, d_sigma,
                                                d_reps, n_reps);
+  return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
+}
+
+int launch_vss_tables_grid(Plan& p, const double* d_fcoef, double2* d_phi, const double* d_gj, int n_alpha, int n_t,
+                           const VssGrid& gr, const int* d_grid_of_pair, const double* d_sigma, const int* d_reps,
+                           int n_reps) {
+  const size_t cells = size_t(gr.np) * gr.nq;
+  for (int a = 0; a < n_alpha; ++a) {
+    const unsigned blocks = unsigned(cells / 256 + 1 < 65536 ? cells / 256 + 1 : 65536);
+    phi_grid_kernel<<<blocks, 256, 0, p.home>>>(d_phi + a * cells, gr.np, gr.nq, gr.p0, gr.q0, gr.h,
+                                                d_gj + size_t(a) * 3 * n_t, n_t);
+  }
+  const size_t N3 = size_t(p.N) * p.N * p.N;
+  const size_t n = size_t(p.s) * p.s * p.N_rho * n_reps * N3;
+  const unsigned blocks = unsigned(n / 256 + 1 < 65536 ? n / 256 + 1 : 65536);
+  vss_from_phi_kernel<<<blocks, 256, 0, p.home>>>(p.d_Fv, p.s * p.s, p.N_rho, p.N, d_fcoef, d_phi, d_grid_of_pair,
+                                                  gr.np, gr.nq, gr.p0, gr.q0, gr.h, d_sigma, d_reps, n_reps);
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
 

@@ -197,6 +197,15 @@ const char* dgfs_strerror(int code);
  * wait for its MMAs gave up. */
 int dgfs_dft3_bf16x3(int N, int dir, const void* x_dev, void* y_dev, int count, void* stream);
 
+/* Self-check of the bounded device-side wait that the DGFS_BF16X3 kernels use for their MMAs
+ * and bulk copies (no counterpart in the paper; failure detection).  One CTA waits on an
+ * mbarrier that nothing completes, giving up after `seconds` (0 < seconds <= 10) of SM clock
+ * at the device's reported clock rate.  Returns DGFS_ERR_DEVICE_TIMEOUT when the wait gave up
+ * and reported it, as designed, and leaves the context usable; DGFS_OK would mean the wait
+ * returned without the barrier completing.  Synchronous; allocates 4 bytes.  Errors:
+ * DGFS_ERR_INVALID_ARG, DGFS_ERR_OOM, DGFS_ERR_CUDA. */
+int dgfs_check_bounded_wait(double seconds);
+
 /* Measured multiply-add rate of the current device's FP32 (precision = DGFS_FP32) or FP64
  * (DGFS_FP64) pipe, in flop/s (2 flop per FMA): the denominator of the ALU roofline that bounds
  * the collision kernel.  No counterpart in the paper (a measurement helper).  Runs a

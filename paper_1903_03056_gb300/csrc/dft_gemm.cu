@@ -375,6 +375,19 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, GemmGeo<N>::MINB)
   if (t < 32) tc::tmem_dealloc(cta.tmem, G::TMEM_COLS);
 }
 
+// One CTA waits, with the tensor-core kernels' bounded wait, on an mbarrier that nothing
+// completes; the wait must give up after `limit_cycles` and report it in *status.
+__global__ void bounded_wait_check_kernel(long long limit_cycles, unsigned* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = tc::mbar_wait_bounded(&bar, 0, limit_cycles);
+  if (!ok && threadIdx.x == 0) atomicOr(status, 1u);
+}
+
 // ---- host: matrix images ---------------------------------------------------------------
 
 constexpr double kPiD = 3.141592653589793238462643383279502884;
@@ -572,6 +585,32 @@ int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t
 }
 
 }  // namespace dgfs
+
+extern "C" int dgfs_check_bounded_wait(double seconds) {
+  if (!(seconds > 0.0) || seconds > 10.0) return DGFS_ERR_INVALID_ARG;
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_CUDA;
+  }
+  unsigned* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return DGFS_ERR_OOM;
+  }
+  unsigned host = 0;
+  int rc = DGFS_OK;
+  const long long cycles = (long long)(seconds * double(khz) * 1e3);
+  if (cudaMemset(d, 0, sizeof(unsigned)) != cudaSuccess) rc = DGFS_ERR_CUDA;
+  if (rc == DGFS_OK) {
+    dgfs::bounded_wait_check_kernel<<<1, 32>>>(cycles, d);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(&host, d, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = DGFS_ERR_CUDA;
+  }
+  cudaFree(d);
+  if (rc != DGFS_OK) return rc;
+  return host != 0 ? DGFS_ERR_DEVICE_TIMEOUT : DGFS_OK;
+}
 
 extern "C" int dgfs_dft3_bf16x3(int N, int dir, const void* x_dev, void* y_dev, int count, void* stream) {
   if (count < 0 || (dir != 1 && dir != -1)) return DGFS_ERR_INVALID_ARG;

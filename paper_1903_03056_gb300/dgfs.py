@@ -41,7 +41,7 @@ EXPORTS = ("dgfs_create_plan", "dgfs_destroy_plan", "dgfs_eval_collision",
            "dgfs_plan_launches", "dgfs_plan_check", "dgfs_strerror", "dgfs_eval_collision_noalloc",
            "dgfs_plan_set_sm_share", "dgfs_ssp_rk2_step", "dgfs_dg_create", "dgfs_dg_destroy",
            "dgfs_dg_nodes", "dgfs_dg_transport", "dgfs_dg_step", "dgfs_measure_fma_rate",
-           "dgfs_dft3_bf16x3")
+           "dgfs_dft3_bf16x3", "dgfs_check_bounded_wait")
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -97,6 +97,7 @@ def load():
     lib.dgfs_dg_step.argtypes = [vp, vp, ctypes.c_double, vp]
     lib.dgfs_measure_fma_rate.argtypes = [ci, _dptr]
     lib.dgfs_dft3_bf16x3.argtypes = [ci, ci, vp, vp, ci, vp]
+    lib.dgfs_check_bounded_wait.argtypes = [ctypes.c_double]
     lib.dgfs_strerror.argtypes = [ci]
     lib.dgfs_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -218,6 +219,10 @@ def precision_code(precision):
     if precision in (DGFS_FP64, DGFS_FP32, DGFS_BF16X3):
         return int(precision)
     raise ValueError("unknown precision %r" % (precision,))
+
+
+def dgfs_check_bounded_wait(seconds):
+    return load().dgfs_check_bounded_wait(float(seconds))
 
 
 def dgfs_dft3_bf16x3(N, direction, x_dev, y_dev, count, stream):

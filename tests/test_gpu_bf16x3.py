@@ -127,3 +127,16 @@ def test_bf16x3_full_hs_batch_sampled_nodes():
     print("hs_n24 bf16x3: error vs oracle per node %.3e, vs the FP32 path over the batch %.3e" % (err, err32))
     assert err < TOL_FP32
     assert err32 < 2 * TOL_FP32
+
+
+def test_bounded_wait_gives_up_and_reports():
+    """The tensor-core kernels' wait on an mbarrier gives up after its limit and reports the
+    timeout instead of hanging; the context stays usable afterwards."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    assert dgfs.dgfs_check_bounded_wait(0.05) == dgfs.DGFS_ERR_DEVICE_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    x = torch.ones(8, device="cuda")
+    assert float((x * 2).sum()) == 16.0
+    assert dgfs.dgfs_check_bounded_wait(0.0) == dgfs.DGFS_ERR_INVALID_ARG

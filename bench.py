@@ -386,6 +386,52 @@ def fp64_serving_replay(ex, stream, measured, chunk, policy, spn32, budget):
             "fp64_over_fp32_device_work": work64 / work32}
 
 
+def bf16x3_tensor_flops_per_node(w):
+    """BF16 tensor-core work of one node on the DGFS_BF16X3 path: every 3D transform is 3 passes
+    over ceil(N^2 / 128) tiles of 128 lines, 6 split-term products of 2 x 128 x 2N x 2N flop.
+    Transforms per node (antipodal rule): a self-pair task does its f_hat, 2 (M/2) N_rho shifted
+    transforms, N_rho forward transforms of P and 2 final ones; a cross-pair task 2 f_hat,
+    2 M N_rho shifted, N_rho forward and 4 final."""
+    s, M, NR, N = w.s, w.M, w.N_rho, w.N
+    self_t = 1 + 2 * (M // 2) * NR + NR + 2
+    cross_t = 2 + 2 * M * NR + NR + 4
+    transforms = s * self_t + s * (s - 1) // 2 * cross_t
+    tiles = (N * N + 127) // 128
+    return transforms, transforms * 3 * tiles * 6 * 2 * 128 * (2 * N) * (2 * N)
+
+
+def tensor_leg(torch, stream, steps=3):
+    """The split-BF16 tensor-core path against the FP32 FFT kernel on the 16384-node N = 24
+    hard-sphere batch (the workload that path is defined on), same inputs, CUDA events."""
+    from paper_1903_03056_gb300 import dgfs, synth
+    w = synth.WORKLOADS["hs_n24"]
+    f = synth.batch_distribution(w)
+    with torch.cuda.stream(stream):
+        fd = torch.from_numpy(f.astype(np.float32)).cuda()
+        Q = torch.empty((w.batch, w.s, w.s, w.N, w.N, w.N), dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    out = {"config": {"workload": w.name, "batch": w.batch, "N": w.N, "species": w.s, "masses": list(w.masses),
+                      "omega": w.omega, "M": w.M, "N_rho": w.N_rho}}
+    for prec in ("fp32", "bf16x3"):
+        plan = dgfs.Plan(w.N, w.L, list(w.masses), w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho, precision=prec)
+        ms = time_steps(torch, lambda: plan.eval_ptr(fd.data_ptr(), Q.data_ptr(), w.batch, stream), steps, 1, stream)
+        out[prec] = {"ms_per_step": ms, "evals_per_s": w.batch / (ms * 1e-3)}
+        plan.close()
+    transforms, flops = bf16x3_tensor_flops_per_node(w)
+    achieved = flops * w.batch / (out["bf16x3"]["ms_per_step"] * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, how = float(json.load(fh)["bf16_tflops_sustained"]), "measured, sustained"
+    except (OSError, ValueError, KeyError):
+        peak, how = 1700.0, "fallback, sustained"
+    out["bf16x3"]["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": achieved / peak, "peak_source": how, "transforms_per_node": transforms,
+                                 "tensor_flops_per_node": flops, "kernel": "gemm_collision_kernel<24>"}
+    out["bf16x3_over_fp32"] = out["bf16x3"]["evals_per_s"] / out["fp32"]["evals_per_s"]
+    del fd, Q
+    return out
+
+
 def dg_leg(torch, w, stream, Ne=1024, K=4):
     """The 1D DG path on Ne elements of K GLL nodes (Ne K = 4096 nodes of the batch's grid and
     species) between Maxwell walls: one transport pass (HBM-bound kernel, algorithmic bytes = the
@@ -504,6 +550,10 @@ def gpu_arm(args):
     if not args.no_dg and world == 1:
         dg = dg_leg(torch, w, stream)
 
+    tensor = None
+    if not args.no_tensor and world == 1:
+        tensor = tensor_leg(torch, stream)
+
     serving = None
     if not args.no_serving and world == 1:
         del f32
@@ -529,7 +579,9 @@ def gpu_arm(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_dict(w), "roofline": roof,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "fp64": fp64, "dg": dg, "serving": serving}
+                "clocks": clk.summary(), "fp64": fp64, "dg": dg, "tensor_path": tensor, "serving": serving,
+                "parity": {"fp32_bar": "1e-5 of the node's max |Q| over its s^2 operators (per-node scale) "
+                                       "against the FP64 oracle", "fp64_bar": "1e-11 of max |Q| per pair"}}
         print(json.dumps(line), flush=True)
     plan32.close()
     if dist is not None:
@@ -547,6 +599,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-dg", action="store_true")
+    ap.add_argument("--no-tensor", action="store_true", help="skip the split-BF16 tensor-core leg")
     ap.add_argument("--serve-calib", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-sm-share", type=float, default=1.0)

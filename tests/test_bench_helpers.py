@@ -72,3 +72,22 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     monkeypatch.setenv("RANK", "1")
     assert bench.reference_arm(argparse.Namespace(gpus=2, steps=1, warmup=0)) is None
     assert capsys.readouterr().out == ""
+
+
+def test_bf16x3_tensor_work_counts_the_kernels_transforms():
+    """The tensor-core kernel recomputes f_hat per task (one per species of the task), does two
+    shifted transforms per entry and radial node (self pairs: half the directions), one forward
+    transform of the product sum per radial node, and a loss and a gain transform per output
+    pair; every transform is 3 passes of ceil(N^2/128) tiles x 6 split products of
+    2 x 128 x 2N x 2N flop."""
+    w = synth.WORKLOADS["hs_n24"]
+    n = 0
+    for i in range(w.s):
+        for j in range(i, w.s):
+            nspec = 1 if i == j else 2
+            entries = w.M // 2 if i == j else w.M
+            outputs = 1 if i == j else 2
+            n += nspec + 2 * entries * w.N_rho + w.N_rho + 2 * outputs
+    transforms, flops = bench.bf16x3_tensor_flops_per_node(w)
+    assert transforms == n == 624
+    assert flops == n * 3 * math.ceil(w.N * w.N / 128) * 6 * 2 * 128 * (2 * w.N) ** 2

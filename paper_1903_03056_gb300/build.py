@@ -2,8 +2,9 @@
 
     python -m paper_1903_03056_gb300.build [--force] [--verbose]
 
-Translation units compile in parallel; the library is rebuilt only when a source or header
-is newer than it.  ptxas resource usage (registers, spills, shared memory) is written to
+Translation units compile in parallel; the library is rebuilt when the SHA-1 of its sources,
+headers and build flags differs from the one recorded at its last build (or the library is
+missing).  ptxas resource usage (registers, spills, shared memory) is written to
 ``_build/ptxas.log`` beside the objects.
 """
 
@@ -38,11 +39,24 @@ def _deps():
     return files
 
 
+STAMP = os.path.join(BUILD, "sources.sha1")
+
+
+def sources_sha1():
+    """SHA-1 over every source and header of the library and the compile flags."""
+    import hashlib
+    h = hashlib.sha1(" ".join(ARCH + FLAGS + SOURCES).encode())
+    for f in sorted(_deps()):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    with open(STAMP) as fh:
+        return fh.read().strip() == sources_sha1()
 
 
 def _compile(src):
@@ -76,6 +90,8 @@ def build(force=False, verbose=False):
         sys.stderr.write(res.stdout + res.stderr)
         raise RuntimeError("link failed")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(sources_sha1() + "\n")
     if verbose:
         print("built", LIB)
     return LIB

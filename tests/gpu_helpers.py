@@ -70,3 +70,16 @@ def check(Q_gpu, Q_ref, precision):
     if precision == "fp64":
         return max_rel_error(Q_gpu, Q_ref, "pair") < TOL_FP64
     return max_rel_error(Q_gpu, Q_ref, "node") < TOL_FP32
+
+
+def oracle_node_of_workload(args):
+    """(workload key, node) -> the oracle's Q of that node of the seeded workload (for spawned
+    worker processes: single-threaded BLAS, imports inside)."""
+    import os
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from paper_1903_03056_gb300 import synth
+    key, node = args
+    w = synth.WORKLOADS[key]
+    prob = fs.make_problem(w.N, w.L, list(w.masses), omega=w.omega, alpha=w.alpha, M=w.M, N_rho=w.N_rho)
+    return fs.collision(synth.node_distribution(w, node), prob)[0]

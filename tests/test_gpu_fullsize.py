@@ -13,7 +13,7 @@
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL_FP32, TOL_FP64, max_rel_error
+from gpu_helpers import TOL_FP32, TOL_FP64, max_rel_error, oracle_node_of_workload
 from oracle import fast_spectral as fs
 from paper_1903_03056_gb300 import build, dgfs, synth
 
@@ -45,7 +45,7 @@ def _oracle_nodes(w, f, nodes):
 def _eval(w, f, precision, nodes=None):
     """Evaluate the whole batch (nodes=None) or only the listed nodes; returns a torch tensor."""
     import torch
-    dt = torch.float32 if precision == "fp32" else torch.float64
+    dt = torch.float64 if precision == "fp64" else torch.float32
     plan = _plan(w, precision)
     src = f if nodes is None else f[nodes]
     fd = torch.from_numpy(np.ascontiguousarray(src)).to(device="cuda", dtype=dt)
@@ -99,3 +99,27 @@ def test_vss_n48_full_batch_properties():
     err = max_rel_error(sample.double().numpy(), ref, "node")
     print("vss_n48 fp32 vs fp64 path: per node %.3e" % err)
     assert err < TOL_FP32
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_hs_n24_64_node_subsample_against_the_oracle(precision):
+    """The error of the 16384-node N = 24 batch, evaluated whole in one launch, on its first 64
+    nodes against the oracle (the subsample the workload's error is stated on); the oracle runs
+    in a spawn pool of worker processes."""
+    import multiprocessing as mp
+    import os
+    w = synth.WORKLOADS["hs_n24"]
+    f = _inputs("hs_n24")
+    Q = _eval(w, f, precision)
+    sample = Q[:64].double().cpu().numpy()
+    del Q
+    key = "hs_n24_oracle_64"
+    if key not in _ORACLE_CACHE:
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            _ORACLE_CACHE[key] = np.stack(pool.map(oracle_node_of_workload, [("hs_n24", b) for b in range(64)]))
+    err = max_rel_error(sample, _ORACLE_CACHE[key], "node")
+    print("hs_n24 %s: 64-node subsample, error vs oracle per node %.3e" % (precision, err))
+    assert err < TOL_FP32
+
+
+_ORACLE_CACHE = {}

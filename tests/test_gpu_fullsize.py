@@ -115,8 +115,20 @@ def test_hs_n24_64_node_subsample_against_the_oracle(precision):
     del Q
     key = "hs_n24_oracle_64"
     if key not in _ORACLE_CACHE:
-        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-            _ORACLE_CACHE[key] = np.stack(pool.map(oracle_node_of_workload, [("hs_n24", b) for b in range(64)]))
+        # one BLAS thread per worker: the limits are set before the workers start (they import
+        # numpy on start-up), else every worker's BLAS spawns a thread per core
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+                _ORACLE_CACHE[key] = np.stack(pool.map(oracle_node_of_workload, [("hs_n24", b) for b in range(64)]))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     err = max_rel_error(sample, _ORACLE_CACHE[key], "node")
     print("hs_n24 %s: 64-node subsample, error vs oracle per node %.3e" % (precision, err))
     assert err < TOL_FP32

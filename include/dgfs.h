@@ -141,14 +141,17 @@ int dgfs_eval_collision(dgfs_plan plan, const void* f_dev, void* Q_dev, int batc
 /* The same evaluation from host buffers (pinned or pageable; pinned lets the copies run
  * asynchronously): copies f to the device, evaluates, copies Q back and returns when Q is in
  * host memory.  Batches of 512 nodes or more are split into up to 8 chunks whose input copy,
- * evaluation (on `stream`) and output copy (on two copy streams the plan owns) overlap.
- * batch <= max_batch, else DGFS_ERR_BUDGET.  The plan's staging buffers are allocated at the
- * first call. */
+ * evaluation and output copy (on two copy streams the plan owns) overlap; the chunks'
+ * evaluations alternate between `stream` and a second stream of the plan, each with a
+ * workspace of its own, so one chunk's kernel starts while the previous one ends.  The call
+ * is ordered after the work already on `stream` and after the plan's previous evaluation.
+ * batch <= max_batch, else DGFS_ERR_BUDGET.  The plan's staging buffers and second workspace
+ * are allocated at the first call. */
 int dgfs_eval_collision_host(dgfs_plan plan, const void* f_host, void* Q_host, int batch,
                              void* stream);
 
-/* Device bytes of the plan's tables and workspace (workspace includes host-call staging
- * for `batch` nodes). */
+/* Device bytes of the plan's tables and workspace (with batch > 0 the workspace includes what
+ * a host-buffer call of `batch` nodes adds: staging and the second workspace). */
 int dgfs_plan_bytes(dgfs_plan plan, int batch, size_t* tables, size_t* workspace);
 
 /* The radial truncation R the plan uses (R = 2S from Eq. domain unless given; with

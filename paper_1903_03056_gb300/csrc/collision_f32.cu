@@ -6,10 +6,10 @@
 namespace dgfs {
 
 #define DGFS_CONFIGURE(T, N) configure_impl<T, N>(p)
-#define DGFS_LAUNCH(T, N) launch_impl<T, N>(p, f, Q, batch, st)
+#define DGFS_LAUNCH(T, N) launch_impl<T, N>(p, f, Q, batch, st, ws)
 
 int configure_f32(Plan& p) { DGFS_DISPATCH(float, p.N, DGFS_CONFIGURE) }
-int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws) {
   DGFS_DISPATCH(float, p.N, DGFS_LAUNCH)
 }
 

@@ -628,7 +628,7 @@ int configure_impl(Plan& pl) {
 }
 
 template <typename T, int N>
-int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t st) {
+int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t st, int ws) {
   using G = Geo<T, N>;
   KernelParams kp;
   kp.f = f;
@@ -644,9 +644,9 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   kp.phase = pl.d_phase;
   kp.Fw = pl.d_Fwf ? static_cast<const void*>(pl.d_Fwf) : static_cast<const void*>(pl.d_Fw);
   kp.Gm = pl.d_Gmf ? static_cast<const void*>(pl.d_Gmf) : static_cast<const void*>(pl.d_Gm);
-  kp.scratch = pl.d_scratch;
+  kp.scratch = pl.scratch_of(ws);
   kp.phase_smem = pl.shape.phase_smem;
-  kp.work_counter = pl.d_counter;
+  kp.work_counter = pl.counter_of(ws);
   kp.vss = pl.vss ? 1 : 0;
   kp.n_fslot = pl.n_fslot;
   kp.Fv = pl.d_Fvf ? static_cast<const void*>(pl.d_Fvf) : static_cast<const void*>(pl.d_Fv);
@@ -668,7 +668,7 @@ int launch_impl(const Plan& pl, const void* f, void* Q, int batch, cudaStream_t 
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaMemsetAsync(pl.d_counter, 0, sizeof(unsigned), st) != cudaSuccess) return DGFS_ERR_CUDA;
+  if (cudaMemsetAsync(kp.work_counter, 0, sizeof(unsigned), st) != cudaSuccess) return DGFS_ERR_CUDA;
   if (cudaLaunchKernelEx(&cfg, collision_kernel<T, N>, kp) != cudaSuccess) return DGFS_ERR_CUDA;
   return DGFS_OK;
 }

@@ -464,7 +464,7 @@ int configure_gemm_impl(Plan& p) {
 }
 
 template <int N>
-int launch_gemm_impl(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+int launch_gemm_impl(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws) {
   using G = GemmGeo<N>;
   GemmParams kp;
   kp.f = static_cast<const float*>(f);
@@ -479,14 +479,14 @@ int launch_gemm_impl(const Plan& p, const void* f, void* Q, int batch, cudaStrea
   kp.mats = p.d_mats;
   kp.Fw = p.d_Fwf;
   kp.Gm = p.d_Gmf;
-  kp.scratch = static_cast<float2*>(p.d_scratch);
-  kp.work_counter = p.d_counter;
-  kp.status = p.d_counter + 1;
+  kp.scratch = static_cast<float2*>(p.scratch_of(ws));
+  kp.work_counter = p.counter_of(ws);
+  kp.status = p.counter_of(ws) + 1;
   const int items = batch * kp.n_tasks;
   int limit = int(p.shape.clusters * p.shape.share);
   if (limit < 1) limit = 1;
   const int grid = items < limit ? items : limit;
-  if (cudaMemsetAsync(p.d_counter, 0, sizeof(unsigned), st) != cudaSuccess) return DGFS_ERR_CUDA;
+  if (cudaMemsetAsync(kp.work_counter, 0, sizeof(unsigned), st) != cudaSuccess) return DGFS_ERR_CUDA;
   gemm_collision_kernel<N><<<grid, G::THREADS, G::SMEM, st>>>(kp);
   return cudaPeekAtLastError() == cudaSuccess ? DGFS_OK : (cudaGetLastError(), DGFS_ERR_CUDA);
 }
@@ -575,11 +575,11 @@ int configure_bf16x3(Plan& p) {
   }
 }
 
-int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st) {
+int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws) {
   switch (p.N) {
-    case 8: return launch_gemm_impl<8>(p, f, Q, batch, st);
-    case 16: return launch_gemm_impl<16>(p, f, Q, batch, st);
-    case 24: return launch_gemm_impl<24>(p, f, Q, batch, st);
+    case 8: return launch_gemm_impl<8>(p, f, Q, batch, st, ws);
+    case 16: return launch_gemm_impl<16>(p, f, Q, batch, st, ws);
+    case 24: return launch_gemm_impl<24>(p, f, Q, batch, st, ws);
     default: return DGFS_ERR_UNSUPPORTED_N;
   }
 }

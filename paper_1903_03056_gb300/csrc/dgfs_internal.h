@@ -145,6 +145,15 @@ struct Plan {
   unsigned* d_counter = nullptr;   // work-item counter of the persistent kernel; the next word is
                                    // the device status (set when a bounded device wait gave up)
   uint16_t* d_mats = nullptr;      // DGFS_BF16X3: line-transform matrix images (split BF16)
+  // second workspace and work counter (allocated by the first host-buffer call): consecutive
+  // chunks of a host-buffer evaluation alternate between the two, on two streams, so that one
+  // chunk's kernel starts while the previous one finishes its last work items
+  void* d_scratch2_raw = nullptr;
+  void* d_scratch2 = nullptr;
+  unsigned* d_counter2 = nullptr;
+  cudaStream_t eval2 = nullptr;
+  void* scratch_of(int ws) const { return ws == 0 ? d_scratch : d_scratch2; }
+  unsigned* counter_of(int ws) const { return ws == 0 ? d_counter : d_counter2; }
   size_t scratch_bytes = 0;
   void* d_rk = nullptr;             // SSP-RK2 workspace: f1 and the right-hand side
   void* d_stage_f = nullptr;
@@ -179,8 +188,8 @@ void free_plan(Plan& p);
 // kernel configuration and launch, per precision (collision_f32.cu / collision_f64.cu)
 int configure_f32(Plan& p);
 int configure_f64(Plan& p);
-int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
-int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+int launch_f32(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws = 0);
+int launch_f64(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws = 0);
 
 // on-device FP64 weight tables on the plan's stream (tables.cu)
 int launch_vhs_tables(Plan& p, const double* d_fcoef, const double* d_gcoef, const double* d_gscale, int n_loss);
@@ -208,7 +217,7 @@ int launch_vss_tables_grid(Plan& p, const double* d_fcoef, double2* d_phi, const
 bool gemm_supported_n(int N);
 void build_gemm_images(const Plan& p, const std::vector<std::complex<double>>& phase, std::vector<uint16_t>& out);
 int configure_bf16x3(Plan& p);
-int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st);
+int launch_bf16x3(const Plan& p, const void* f, void* Q, int batch, cudaStream_t st, int ws = 0);
 
 // SSP-RK2 stage combinations (stepper.cu): stage 1 f1 = f + dt r; stage 2 f = (f + f1 + dt r)/2
 int launch_rk_stage(const Plan& p, int stage, void* f, void* f1, const void* r, double dt, size_t n, cudaStream_t st);

@@ -756,7 +756,8 @@ int upload_plan(Plan& p) {
 void free_plan(Plan& p) {
   void* ptrs[] = {p.d_Fw,      p.d_Gm,      p.d_ent_w,   p.d_phase, p.d_tasks, p.d_groups, p.d_Fv,
                   p.d_scratch_raw, p.d_stage_f, p.d_stage_Q, p.d_cons, p.d_kappa, p.d_Qfull, p.d_ent_m,
-                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf,   p.d_mats};
+                  p.d_counter, p.d_rk,      p.d_ent_ysh, p.d_Fwf,    p.d_Fvf,   p.d_Gmf,   p.d_mats,
+                  p.d_scratch2_raw, p.d_counter2};
   if (p.home) {
     for (void* q : ptrs)
       if (q) cudaFreeAsync(q, p.home);
@@ -775,6 +776,10 @@ void free_plan(Plan& p) {
   }
   if (p.ev_start) cudaEventDestroy(p.ev_start);
   if (p.h2d) cudaStreamDestroy(p.h2d);
+  if (p.eval2) cudaStreamDestroy(p.eval2);
+  p.eval2 = nullptr;
+  p.d_scratch2_raw = p.d_scratch2 = nullptr;
+  p.d_counter2 = nullptr;
   if (p.d2h) cudaStreamDestroy(p.d2h);
   p.ev_start = nullptr;
   p.h2d = p.d2h = nullptr;

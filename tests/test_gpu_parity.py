@@ -189,6 +189,32 @@ def test_host_pipeline_chunks_and_sm_share_give_identical_results():
     plan.close()
 
 
+@pytest.mark.parametrize("precision,flags", [("fp32", dgfs.DGFS_SUM_SPECIES | dgfs.DGFS_CONSERVE),
+                                             ("bf16x3", dgfs.DGFS_SUM_SPECIES), ("fp64", 0)])
+def test_host_pipeline_on_two_workspaces_matches_device_evaluation(precision, flags):
+    """A 1100-node host-buffer call runs as 4 chunks that alternate between two evaluation
+    streams and two workspaces, the species sum staging each chunk at its own offset; the
+    result equals the device-resident evaluation bit for bit, both workspaces' guard blocks
+    stay intact, and an evaluation afterwards on the caller's stream is ordered after it."""
+    import torch
+    B = 1100
+    dt = np.float64 if precision == "fp64" else np.float32
+    f = _inputs(8, 4.0, (1.0, 2.0), B, seed=43).astype(dt)
+    plan = dgfs.Plan(8, 4.0, [1.0, 2.0], 0.6, M=6, N_rho=3, precision=precision, max_batch=B, flags=flags)
+    s_out = 2 if flags & dgfs.DGFS_SUM_SPECIES else 4
+    shape = (B, 2, 8, 8, 8) if s_out == 2 else (B, 2, 2, 8, 8, 8)
+    Qh = np.zeros(shape, dtype=dt)
+    plan.eval_host(np.ascontiguousarray(f), Qh)
+    per_chunk = 1 + bool(flags & dgfs.DGFS_CONSERVE) + bool(flags & dgfs.DGFS_SUM_SPECIES)
+    assert plan.launches() == 4 * per_chunk
+    assert plan.check()
+    Qd = plan.eval(torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(Qh, Qd.cpu().numpy())
+    assert plan.check()
+    plan.close()
+
+
 @pytest.mark.parametrize("flags", [0, dgfs.DGFS_CONSERVE])
 def test_cuda_graph_replay_matches_direct_launch(flags):
     """The evaluation (memset of the work counter, persistent kernel, projection) is

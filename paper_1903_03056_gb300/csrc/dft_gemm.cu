@@ -39,7 +39,8 @@ struct GemmParams {
 
 namespace {
 
-template <int N>
+// a CTA's volumes between transforms, in its workspace slot: f_hat_i, f_hat_j, the shifted
+// f_i of the current entry, the two gain accumulators, the loss convolution
 struct Vol {
   float2 *FI, *FJ, *AV, *QA, *QB;
   float* LS;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(GemmGeo<N>::THREADS, GemmGeo<N>::MINB) gemm_co
   const size_t img = size_t(G::B_ELEMS);
   const uint16_t* fwd = p.mats + size_t(p.n_tasks) * p.n_rho * p.max_ent * 6 * img;
   const uint16_t* inv = fwd + img;
-  Vol<N> V;
+  Vol V;
   float2* scr = p.scratch + size_t(blockIdx.x) * 6 * N3;
   V.FI = scr;
   V.FJ = scr + N3;

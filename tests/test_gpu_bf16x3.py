@@ -140,3 +140,53 @@ def test_bounded_wait_gives_up_and_reports():
     x = torch.ones(8, device="cuda")
     assert float((x * 2).sum()) == 16.0
     assert dgfs.dgfs_check_bounded_wait(0.0) == dgfs.DGFS_ERR_INVALID_ARG
+
+
+def test_bf16x3_graph_replay_matches_direct_launch():
+    """The tensor-core evaluation (counter reset, kernel) is stream-ordered and capturable: a
+    replayed CUDA graph computes the same bits as the direct launch, also after the input
+    changes in place."""
+    import torch
+    f = torch.from_numpy(_inputs(16, 6.0, (1.0, 2.0), 3, seed=351)).float().cuda()
+    plan = dgfs.Plan(16, 6.0, [1.0, 2.0], 0.5, M=12, N_rho=4, precision="bf16x3")
+    Q = torch.empty((3, 2, 2, 16, 16, 16), dtype=torch.float32, device="cuda")
+    g = plan.capture(f, Q)
+    for k in range(2):
+        f.mul_(1.0 + 0.5 * k)
+        ref = plan.eval(f).clone()
+        Q.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(Q, ref)
+    assert plan.check()
+    plan.close()
+
+
+def test_bf16x3_per_pair_truncation_and_loss_rule_against_oracle():
+    """Ordered-pair tasks with their own radial rules (DGFS_PER_PAIR_R) and the loss weight's
+    own radial rule (DGFS_LOSS_ACCURATE) through the tensor-core precision."""
+    kw = dict(N=8, L=4.0, masses=(1.0, 3.0), omega=0.7, M=6, N_rho=3)
+    f = _inputs(8, 4.0, (1.0, 3.0), 2, seed=355)
+    Q = gpu_collision(f, precision="bf16x3", flags=dgfs.DGFS_PER_PAIR_R | dgfs.DGFS_LOSS_ACCURATE, **kw)
+    ref = oracle_collision(f, pair_radius=True, loss_rule="accurate", **kw)
+    assert max_rel_error(Q, ref, "node") < TOL_FP32
+
+
+def test_bf16x3_ssp_rk2_step_against_oracle():
+    """One homogeneous SSP-RK2 step (two species-summed evaluations and the stage kernels) with a
+    tensor-core plan, against the oracle's step, at the FP32 bar of the step's change."""
+    import torch
+    from oracle import fast_spectral as fs, homogeneous
+    N, L, masses = 8, 4.0, [1.0, 2.0]
+    kappa = np.array([[1.0, 0.8], [1.3, 1.0]])
+    f = _inputs(N, L, masses, 2, seed=357)
+    plan = dgfs.Plan(N, L, masses, 0.6, M=6, N_rho=3, precision="bf16x3", kappa=kappa,
+                     flags=dgfs.DGFS_SUM_SPECIES, max_batch=2)
+    fd = torch.from_numpy(f.astype(np.float32)).cuda()
+    plan.ssp_rk2_step(fd, 0.05)
+    torch.cuda.synchronize()
+    plan.close()
+    prob = fs.make_problem(N, L, masses, omega=0.6, M=6, N_rho=3)
+    ref = np.stack([homogeneous.ssp_rk2_step(fb, 0.05, homogeneous.collision_rhs(prob, kappa)) for fb in f])
+    change = np.max(np.abs(ref - f))
+    assert np.max(np.abs(fd.cpu().numpy() - ref)) < 1e-4 * change + 1e-6 * np.max(np.abs(ref))

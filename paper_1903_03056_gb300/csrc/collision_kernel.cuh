@@ -27,6 +27,7 @@
 
 #include "dgfs_internal.h"
 #include "fft_line.cuh"
+#include "tcgen05.cuh"
 
 namespace dgfs {
 
@@ -77,6 +78,11 @@ struct Geo {
   // L2 prefetch of the workspace reads (measured: a gain from N = 24 on, where the clusters'
   // workspaces together exceed L2; a loss at N = 16); bulk prefetches need whole 16-byte rows
   static constexpr bool PF = N >= 24 && (PENCILS * sizeof(C<T>)) % 16 == 0;
+  // staged plane pass (step B): the two plane buffers of a group take turns receiving the next
+  // shifted plane by a bulk copy, issued one (entry, role) ahead of its use, so the plane's
+  // L2/HBM latency overlaps the transforms of the previous role instead of stalling the loads
+  // (P in registers, no y-pass sharing, N >= 24; a plane is a whole number of 16-byte rows)
+  static constexpr bool STAGE = PREG && !YSH && N >= 24 && (N2 * sizeof(C<T>)) % 16 == 0 && (BUF % 16) == 0;
   // workspace volumes per cluster: f_hat_i, f_hat_j, two double-buffered pairs of shifted
   // volumes, two P volumes (the second used by the VSS pipeline), two gain accumulators
   static constexpr int SLOT = 10;
@@ -118,6 +124,13 @@ template <typename T> __device__ __forceinline__ void st2(C<T>* p, C<T> v) { __s
 // read in the next.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Order this thread's generic-proxy accesses to global memory before later async-proxy (bulk
+// copy) accesses: the workspace planes are written with ordinary stores and read back by bulk
+// copies after a barrier.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 
@@ -252,6 +265,45 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
   // the current one, when every CTA has read the current value.
   __shared__ int s_next_item;
   const int n_items = p.batch * p.n_tasks;
+
+  // Staged plane pass: one mbarrier per plane buffer of each group (tb = buffer 0, ab =
+  // buffer 1), armed by the group's first thread for one bulk copy of N^2 complex values.
+  // Every thread of the group keeps the same bookkeeping: fill_par bit b is the parity of
+  // buffer b's next completion, fill_out bit b a copy in flight.  A wait gives up after about
+  // a second: the status word beside the work counter records it, and the group stops issuing
+  // and waiting (its results are then invalid, which the status reports).
+  __shared__ __align__(8) uint64_t s_fill[2 * GP];
+  unsigned fill_par = 0, fill_out = 0;
+  bool stalled = false;
+  if constexpr (G::STAGE) {
+    if (tid == 0) {
+      for (int b = 0; b < 2 * GP; ++b) tc::mbar_init(&s_fill[b], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // start a bulk copy of the plane at src into buffer bi (called by every thread of the group
+  // after the buffer's last readers have passed a group barrier behind a proxy fence)
+  auto fill = [&](int bi, const CT* src) {
+    if (stalled) return;
+    if (t == 0) {
+      uint64_t* bar = &s_fill[2 * grp + bi];
+      tc::mbar_expect_tx(bar, unsigned(N2 * sizeof(CT)));
+      tc::bulk_g2s(bi ? ab : tb, src, unsigned(N2 * sizeof(CT)), bar);
+    }
+    fill_out |= 1u << bi;
+  };
+  auto wait_fill = [&](int bi) {
+    if (stalled) return;
+    if (tc::mbar_wait_bounded(&s_fill[2 * grp + bi], (fill_par >> bi) & 1u, 2000000000LL)) {
+      fill_par ^= 1u << bi;
+      fill_out &= ~(1u << bi);
+    } else {
+      stalled = true;
+      atomicOr(p.work_counter + 1, 2u);
+    }
+  };
+
   if (rank == 0 && tid == 0) s_next_item = int(atomicAdd(p.work_counter, 1u));
   cluster_sync<CL>();
   for (int item = CL == 1 ? s_next_item : ld_rank0(&s_next_item); item < n_items;
@@ -310,6 +362,18 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
       const CT* const phb = ph_smem && !ph_zonly ? phs : phq;  // x and y phases
       const int n_phase = tk.n_grp + (vss ? 2 : 1);
       for (int k = 0; k < n_phase; ++k) {
+        if constexpr (G::STAGE) {
+          // step B of this phase starts on planes written before the last cluster barrier:
+          // copy the first entry's two planes now, so that they land during step A
+          if (k > 0 && k <= tk.n_grp) {
+            fence_proxy_async_global();
+            tc::fence_async_smem();
+            group_sync<N, GP>();
+            const size_t x0 = size_t(plane0 + grp) * N2;
+            fill(0, (((k - 1) & 1) ? HA1 : HA0) + x0);
+            fill(1, (((k - 1) & 1) ? HB1 : HB0) + x0);
+          }
+        }
         if (k < tk.n_grp) {
           const GroupDesc gd = p.groups[tk.grp_off + k];
           CT* const dA = (k & 1) ? HA1 : HA0;
@@ -333,8 +397,96 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
 #pragma unroll
             for (int n = 0; n < N; ++n) st2<T>(dst + n * N2 + pp, v[n]);
           }
+          // the next phase reads these planes with bulk copies
+          if constexpr (G::STAGE) fence_proxy_async_global();
         }
-        if (k > 0 && k <= tk.n_grp) {
+        if (G::STAGE && k > 0 && k <= tk.n_grp) {
+          const int gi = k - 1;
+          const GroupDesc gd = p.groups[tk.grp_off + gi];
+          const CT* const sA = (gi & 1) ? HA1 : HA0;
+          const CT* const sB = (gi & 1) ? HB1 : HB0;
+          const bool last = vss || gi == tk.n_grp - 1;
+          const bool fresh = vss || gi == 0;
+          CT* const PVw = (vss && (gi & 1)) ? PV1 : PV;
+          const int e_end = gd.first + gd.count;
+          // staged step B.  Role 0 of an entry reads buffer `cur` and leaves a_e in it; role 1
+          // reads the other buffer.  After role 1's transpose its buffer takes the next
+          // entry's role-0 plane; after the product, `cur` takes the next entry's role-1 plane.
+          // Every entry of the group reads the same two planes (the x pass is shared).
+          int cur = 0;
+          for (int xl = grp; xl < G::PLANES; xl += GP) {
+            const int x = plane0 + xl;
+            CT P[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) P[c] = fresh ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
+            for (int e = gd.first; e < e_end; ++e) {
+              const T w = T(p.ent_w[tk.ent_off + e]);
+              CT v[N];
+#pragma unroll 1
+              for (int role = 0; role < 2; ++role) {
+                const int bi = role == 0 ? cur : 1 - cur;
+                CT* const B = bi ? ab : tb;
+                const CT* phy = phb + ((e * 2 + role) * 3 + 1) * N;
+                const CT* phz = phb + ((e * 2 + role) * 3 + 2) * N;
+                wait_fill(bi);
+                // column t of the plane as copied (unpadded rows), with the y phase
+#pragma unroll
+                for (int r = 0; r < N; ++r) v[r] = cmul<T>(B[r * N + t], phy[r]);
+                group_sync<N, GP>();  // every column read: the buffer is re-laid out in place
+#pragma unroll 1
+                for (int pass = 0; pass < 2; ++pass) {
+                  if (pass == 1) {
+#pragma unroll
+                    for (int r = 0; r < N; ++r) B[r * PITCH + t] = v[r];
+                    group_sync<N, GP>();
+#pragma unroll
+                    for (int c = 0; c < N; ++c) v[c] = cmul<T>(B[t * PITCH + c], phz[c]);
+                    if (role == 1) {
+                      // the buffer is free: the next entry's role-0 plane
+                      const CT* nxt = e + 1 < e_end ? sA + size_t(x) * N2
+                                    : xl + GP < G::PLANES ? sA + size_t(x + GP) * N2 : nullptr;
+                      tc::fence_async_smem();
+                      group_sync<N, GP>();
+                      if (nxt != nullptr) fill(bi, nxt);
+                    }
+                  }
+                  fft_line<T, N, +1>(v);
+                }
+                if (role == 0) {
+#pragma unroll
+                  for (int c = 0; c < N; ++c) B[t * PITCH + c] = v[c];
+                }
+              }
+              const CT* A0 = cur ? ab : tb;
+#pragma unroll
+              for (int c = 0; c < N; ++c) {
+                const CT ab_ = cmul<T>(A0[t * PITCH + c], v[c]);
+                P[c] = mk<T>(P[c].x + w * ab_.x, P[c].y + w * ab_.y);
+              }
+              if (e + 1 < e_end) {
+                tc::fence_async_smem();
+                group_sync<N, GP>();
+                fill(cur, sB + size_t(x) * N2);
+              }
+              cur = 1 - cur;
+            }
+            // the last entry's role-0 buffer (1 - cur) is free once every row has been read
+            CT* const Pb = cur ? tb : ab;
+            if (last) {
+              plane_pass2<T, N, GP, -1, false>(P, Pb, t, nullptr);
+#pragma unroll
+              for (int r = 0; r < N; ++r) st2<T>(PVw + x * N2 + r * N + t, P[r]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < N; ++c) st2<T>(PV + x * N2 + c * N + t, P[c]);
+            }
+            if (xl + GP < G::PLANES) {
+              tc::fence_async_smem();
+              group_sync<N, GP>();
+              fill(1 - cur, sB + size_t(x + GP) * N2);
+            }
+          }
+        } else if (k > 0 && k <= tk.n_grp) {
           const int gi = k - 1;
           const GroupDesc gd = p.groups[tk.grp_off + gi];
           const CT* const sA = (gi & 1) ? HA1 : HA0;
@@ -575,6 +727,13 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         group_sync<N, GP>();
       }
       cluster_sync<CL>();
+    }
+  }
+  // a group that gave up waiting lets its copies in flight land (bounded) before it leaves
+  if constexpr (G::STAGE) {
+    if (stalled && t == 0) {
+      for (int b = 0; b < 2; ++b)
+        if ((fill_out >> b) & 1u) tc::mbar_wait_bounded(&s_fill[2 * grp + b], (fill_par >> b) & 1u, 2000000000LL);
     }
   }
   // no CTA leaves while another may still read its shared memory (the last item index)

@@ -72,8 +72,21 @@ struct Geo {
   // 8192-node N = 16 batch: FP32 -4 %, FP64 -11 %; at N = 24 and 32 the third buffer takes
   // the room of the phase block and of L1 and the kernel ran 5-8 % slower, so it stays off.
   static constexpr bool YSH = N <= 16 && PREG && RES * (GP * 3 * BUF + 1024 + 8 * 1024) <= 228 * 1024;
-  // smem planes per plane group: transpose (role 0), a, then P (!PREG) or the role-1 transpose
-  static constexpr int NBUF = (PREG && !YSH) ? 2 : 3;
+  // Tensor-memory accumulators: the sigma sum P of each of a group's planes and the role-0 line
+  // a_e live in TMEM columns (2N FP32 columns per line) instead of registers and shared memory,
+  // which leaves the registers to the line transform and keeps P on chip across the sigma_x
+  // groups of a radial node.  FP32, groups of one whole warp and at most 128 threads (each
+  // thread owns one TMEM lane), and the allocations of the CTAs an SM holds within its 512
+  // columns.
+  static constexpr int PPG = PLANES / GP;  // planes per group
+  static constexpr int TM_COLS = 2 * N * (PPG + 1);
+  static constexpr int TM_ALLOC =
+      TM_COLS <= 32 ? 32 : TM_COLS <= 64 ? 64 : TM_COLS <= 128 ? 128 : TM_COLS <= 256 ? 256 : 512;
+  static constexpr bool TM = sizeof(T) == 4 && N % 32 == 0 && THREADS <= 128 && !YSH &&
+                             TM_COLS <= 512 && RES * TM_ALLOC <= 512;
+  // smem planes per plane group: transpose (role 0), a, then P (!PREG) or the role-1 transpose;
+  // with TMEM accumulators the transpose buffer only
+  static constexpr int NBUF = TM ? 1 : (PREG && !YSH) ? 2 : 3;
   static constexpr size_t SMEM = size_t(GP) * NBUF * BUF;
   // L2 prefetch of the workspace reads (measured: a gain from N = 24 on, where the clusters'
   // workspaces together exceed L2; a loss at N = 16); bulk prefetches need whole 16-byte rows
@@ -81,17 +94,30 @@ struct Geo {
   // staged plane pass (step B): the two plane buffers of a group take turns receiving the next
   // shifted plane by a bulk copy, issued one (entry, role) ahead of its use, so the plane's
   // L2/HBM latency overlaps the transforms of the previous role instead of stalling the loads
-  // (P in registers, no y-pass sharing, N >= 24; a plane is a whole number of 16-byte rows)
-  static constexpr bool STAGE = PREG && !YSH && N >= 24 && (N2 * sizeof(C<T>)) % 16 == 0 && (BUF % 16) == 0;
-  // workspace volumes per cluster: f_hat_i, f_hat_j, two double-buffered pairs of shifted
-  // volumes, two P volumes (the second used by the VSS pipeline), two gain accumulators
-  static constexpr int SLOT = 10;
+  // (P in registers, no y-pass sharing or TMEM accumulators, N >= 24; a plane is a whole
+  // number of 16-byte rows)
+  static constexpr bool STAGE = !TM && PREG && !YSH && N >= 24 && (N2 * sizeof(C<T>)) % 16 == 0 && (BUF % 16) == 0;
+  // Buffers of the shifted-volume pair: three for clusters of several CTAs, whose VHS phases
+  // split the cluster barrier (a CTA arrives when its step A is written and waits at the end
+  // of the phase, so a CTA may still read pair k-1 while another writes pair k+1), two otherwise.
+  static constexpr int NBV = CL > 1 ? 3 : 2;
+  // workspace volumes per cluster: f_hat_i, f_hat_j, the NBV pairs of shifted volumes, two P
+  // volumes (the second used by the VSS pipeline), two gain accumulators
+  static constexpr int SLOT = 2 + 2 * NBV + 4;
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
+}
+
+// the two halves of the cluster barrier (CL > 1)
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 template <int CL>
@@ -184,6 +210,45 @@ __device__ __forceinline__ void rows_to_cols(C<T> (&x)[N], C<T>* tb, int t) {
   group_sync<N, GP>();
 }
 
+// A line of N complex FP32 values in 2N consecutive TMEM columns of the thread's lane (16
+// columns per access; every thread of the warp takes part).  The load waits for its data inside
+// the same asm statement, so no use of the registers can move ahead of the wait.
+__device__ __forceinline__ void tm_ld16w(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int N>
+__device__ __forceinline__ void tm_store_line(uint32_t ta, const C<float> (&v)[N]) {
+#pragma unroll
+  for (int ch = 0; ch < N / 8; ++ch) {
+    float f[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      f[2 * j] = v[8 * ch + j].x;
+      f[2 * j + 1] = v[8 * ch + j].y;
+    }
+    tc::tmem_st16(ta + uint32_t(16 * ch), f);
+  }
+}
+template <int N>
+__device__ __forceinline__ void tm_load_line(uint32_t ta, C<float> (&v)[N]) {
+#pragma unroll
+  for (int ch = 0; ch < N / 8; ++ch) {
+    float f[16];
+    tm_ld16w(ta + uint32_t(16 * ch), f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[8 * ch + j] = mk<float>(f[2 * j], f[2 * j + 1]);
+  }
+}
+
 // Two-pass transform of a plane: the first line pass, the transpose (columns to rows when
 // COLS_FIRST, rows to columns otherwise), an optional per-element phase, the second line pass.
 // For N >= 32 the passes run as a two-trip loop over one copy of the unrolled line transform,
@@ -245,14 +310,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
   CT* scr = reinterpret_cast<CT*>(p.scratch) + size_t(cid) * G::SLOT * N3;
   CT* const FI = scr;
   CT* const FJ = scr + N3;
-  CT* const HA0 = scr + 2 * N3;
-  CT* const HB0 = scr + 3 * N3;
-  CT* const HA1 = scr + 4 * N3;
-  CT* const HB1 = scr + 5 * N3;
-  CT* const PV = scr + 6 * N3;
-  CT* const PV1 = scr + 7 * N3;
-  CT* const QA = scr + 8 * N3;
-  CT* const QB = scr + 9 * N3;
+  CT* const HA0 = scr + 2 * N3;               // shifted volumes of role 0: HA0 + b N^3
+  CT* const HB0 = scr + (2 + G::NBV) * N3;    // and of role 1
+  CT* const PV = scr + (2 + 2 * G::NBV) * N3;
+  CT* const PV1 = PV + N3;
+  CT* const QA = PV + 2 * N3;
+  CT* const QB = PV + 3 * N3;
   const bool vss = p.vss != 0;
   const int plane0 = rank * G::PLANES;
   const int pencil0 = rank * G::PENCILS;
@@ -303,6 +366,21 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
       atomicOr(p.work_counter + 1, 2u);
     }
   };
+
+  // TMEM accumulators: warp 0 allocates the CTA's columns; thread t of warp w reaches lane
+  // 32 (w % 4) + t
+  __shared__ uint32_t s_tmem;
+  uint32_t tm_row = 0;
+  if constexpr (G::TM) {
+    if (tid < 32) {
+      tc::tmem_alloc(&s_tmem, G::TM_ALLOC);
+      tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tm_row = s_tmem + (uint32_t(32 * ((tid / 32) & 3)) << 16);
+  }
 
   if (rank == 0 && tid == 0) s_next_item = int(atomicAdd(p.work_counter, 1u));
   cluster_sync<CL>();
@@ -361,6 +439,13 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
       }
       const CT* const phb = ph_smem && !ph_zonly ? phs : phq;  // x and y phases
       const int n_phase = tk.n_grp + (vss ? 2 : 1);
+      // Split cluster barrier (VHS, CL > 1): the CTA arrives once its step A of the phase is
+      // written and waits at the end of the phase, so its step B covers the other CTAs' lag.
+      // Pair k is written in phase k and read in phase k + 1, so with three buffers the pair
+      // written in phase k + 1 is one that no CTA reads after arriving in phase k.  The VSS
+      // pipeline's step B writes P volumes other CTAs read in the next phase: one full barrier.
+      const bool split = CL > 1 && !vss;
+      const int nbv = split ? 3 : 2;
       for (int k = 0; k < n_phase; ++k) {
         if constexpr (G::STAGE) {
           // step B of this phase starts on planes written before the last cluster barrier:
@@ -370,14 +455,14 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             tc::fence_async_smem();
             group_sync<N, GP>();
             const size_t x0 = size_t(plane0 + grp) * N2;
-            fill(0, (((k - 1) & 1) ? HA1 : HA0) + x0);
-            fill(1, (((k - 1) & 1) ? HB1 : HB0) + x0);
+            fill(0, HA0 + size_t((k - 1) % nbv) * N3 + x0);
+            fill(1, HB0 + size_t((k - 1) % nbv) * N3 + x0);
           }
         }
         if (k < tk.n_grp) {
           const GroupDesc gd = p.groups[tk.grp_off + k];
-          CT* const dA = (k & 1) ? HA1 : HA0;
-          CT* const dB = (k & 1) ? HB1 : HB0;
+          CT* const dA = HA0 + size_t(k % nbv) * N3;
+          CT* const dB = HB0 + size_t(k % nbv) * N3;
           // step A: x-pencils with the group's shared x phase.  The CTA's pencils of f_hat_i
           // and f_hat_j are N rows of PENCILS contiguous elements each; prefetch them first.
           if constexpr (G::PF) {
@@ -400,11 +485,14 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
           // the next phase reads these planes with bulk copies
           if constexpr (G::STAGE) fence_proxy_async_global();
         }
+        if constexpr (CL > 1) {
+          if (split && k < tk.n_grp) cluster_arrive();
+        }
         if (G::STAGE && k > 0 && k <= tk.n_grp) {
           const int gi = k - 1;
           const GroupDesc gd = p.groups[tk.grp_off + gi];
-          const CT* const sA = (gi & 1) ? HA1 : HA0;
-          const CT* const sB = (gi & 1) ? HB1 : HB0;
+          const CT* const sA = HA0 + size_t(gi % nbv) * N3;
+          const CT* const sB = HB0 + size_t(gi % nbv) * N3;
           const bool last = vss || gi == tk.n_grp - 1;
           const bool fresh = vss || gi == 0;
           CT* const PVw = (vss && (gi & 1)) ? PV1 : PV;
@@ -489,8 +577,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         } else if (k > 0 && k <= tk.n_grp) {
           const int gi = k - 1;
           const GroupDesc gd = p.groups[tk.grp_off + gi];
-          const CT* const sA = (gi & 1) ? HA1 : HA0;
-          const CT* const sB = (gi & 1) ? HB1 : HB0;
+          const CT* const sA = HA0 + size_t(gi % nbv) * N3;
+          const CT* const sB = HB0 + size_t(gi % nbv) * N3;
           // step B: (y, z) planes
           const bool last = vss || gi == tk.n_grp - 1;
           const bool fresh = vss || gi == 0;
@@ -500,8 +588,13 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
           if (PF && t == 0) prefetch_l2(sA + size_t(plane0 + grp) * N2, N2 * sizeof(CT));
           for (int xl = grp; xl < G::PLANES; xl += GP) {
             const int x = plane0 + xl;
-            CT P[G::PREG ? N : 1];
-            if constexpr (G::PREG) {
+            // TMEM columns of this plane's P and of a_e (TMEM accumulators)
+            const uint32_t tp = tm_row + uint32_t(((xl - grp) / GP) * 2 * N);
+            const uint32_t ta = tm_row + uint32_t(G::PPG * 2 * N);
+            CT P[G::PREG && !G::TM ? N : 1];
+            if constexpr (G::TM) {
+              // P stays in TMEM from the first group of the radial node to the last
+            } else if constexpr (G::PREG) {
 #pragma unroll
               for (int c = 0; c < N; ++c) P[c] = fresh ? mk<T>(0, 0) : ld2<T>(PV + x * N2 + c * N + t);
             } else {
@@ -563,11 +656,36 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
                   plane_pass2<T, N, GP, +1, true>(v, tb, t, phz);
                 }
                 if (role == 0) {
+                  if constexpr (G::TM) {
+                    __syncwarp();
+                    tm_store_line<N>(ta, v);
+                  } else {
 #pragma unroll
-                  for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
+                    for (int c = 0; c < N; ++c) ab[t * PITCH + c] = v[c];
+                  }
                 }
               }
-              if constexpr (G::PREG) {
+              if constexpr (G::TM) {
+                // P += w a_e b_e in chunks of 8 values (the first entry of the radial node's first
+                // group writes P)
+                const bool p_first = fresh && e == gd.first;
+                __syncwarp();
+                tc::tmem_wait_st();
+#pragma unroll
+                for (int ch = 0; ch < N / 8; ++ch) {
+                  float a16[16], p16[16];
+                  tm_ld16w(ta + uint32_t(16 * ch), a16);
+                  if (!p_first) tm_ld16w(tp + uint32_t(16 * ch), p16);
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    const CT ab_ = cmul<T>(mk<T>(a16[2 * j], a16[2 * j + 1]), v[8 * ch + j]);
+                    // one rounding per update, as P + w ab in registers (P = 0 at the start)
+                    p16[2 * j] = fmaf(w, ab_.x, p_first ? 0.f : p16[2 * j]);
+                    p16[2 * j + 1] = fmaf(w, ab_.y, p_first ? 0.f : p16[2 * j + 1]);
+                  }
+                  tc::tmem_st16(tp + uint32_t(16 * ch), p16);
+                }
+              } else if constexpr (G::PREG) {
 #pragma unroll
                 for (int c = 0; c < N; ++c) {
                   const CT a = ab[t * PITCH + c];
@@ -586,14 +704,20 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             }
             if (last) {
               CT v[N];
+              if constexpr (G::TM) {
+                __syncwarp();
+                tc::tmem_wait_st();
+                tm_load_line<N>(tp, v);
+              } else {
 #pragma unroll
-              for (int c = 0; c < N; ++c) {
-                if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
+                for (int c = 0; c < N; ++c) {
+                  if constexpr (G::PREG) v[c] = P[c]; else v[c] = pb[t * PITCH + c];
+                }
               }
               plane_pass2<T, N, GP, -1, false>(v, tb, t, nullptr);
 #pragma unroll
               for (int r = 0; r < N; ++r) st2<T>(PVw + x * N2 + r * N + t, v[r]);
-            } else {
+            } else if constexpr (!G::TM) {
 #pragma unroll
               for (int c = 0; c < N; ++c) {
                 CT val;
@@ -651,7 +775,11 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
             }
           }
         }
-        cluster_sync<CL>();
+        if constexpr (CL > 1) {
+          if (split && k < tk.n_grp) cluster_wait(); else cluster_sync<CL>();
+        } else {
+          cluster_sync<CL>();
+        }
       }
       if (vss) continue;
       // step C: forward transform of P along x, weight, accumulate
@@ -736,6 +864,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
         if ((fill_out >> b) & 1u) tc::mbar_wait_bounded(&s_fill[2 * grp + b], (fill_par >> b) & 1u, 2000000000LL);
     }
   }
+  if constexpr (G::TM) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid < 32) tc::tmem_dealloc(s_tmem, G::TM_ALLOC);
+  }
   // no CTA leaves while another may still read its shared memory (the last item index)
   if constexpr (CL > 1) cluster_sync<CL>();
 }
@@ -775,6 +909,18 @@ int configure_impl(Plan& pl) {
   if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters <= 0) {
     cudaGetLastError();
     return DGFS_ERR_CUDA;
+  }
+  if constexpr (G::TM) {
+    // The occupancy calculator grants a kernel that allocates tensor memory one CTA per SM.
+    // The registers, the shared memory and the TMEM columns (RES x TM_ALLOC <= 512) hold RES;
+    // clusters beyond what the device co-schedules wait, and the work counter leaves them the
+    // items still open when they start.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return DGFS_ERR_CUDA;
+    const int cap = G::RES * sms / G::CL;
+    if (cap > clusters) clusters = cap;
   }
   pl.shape.cluster = G::CL;
   pl.shape.groups = G::GP;

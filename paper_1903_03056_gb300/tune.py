@@ -45,7 +45,7 @@ CANDIDATES = {
     24: [(2, 4, 3), (2, 12, 1), (1, 8, 2), (2, 4, 2)],
     32: [(2, 4, 1), (4, 4, 1), (1, 8, 1), (2, 8, 1), (2, 2, 2), (4, 2, 1), (8, 2, 1), (8, 4, 1),
          (4, 8, 1), (2, 2, 4), (4, 2, 4), (2, 1, 8), (1, 2, 4), (2, 4, 3), (1, 4, 3), (4, 4, 3),
-         (2, 2, 6)],
+         (2, 2, 6), (8, 4, 3), (4, 4, 2), (8, 4, 2), (8, 4, 4)],
     48: [(2, 4, 1), (2, 3, 1), (1, 4, 1), (2, 2, 2), (4, 4, 1), (4, 2, 1), (8, 2, 1)],
 }
 
@@ -85,8 +85,8 @@ def _patch_radix(text, T, N, line):
 
 def geometry(N, C, GP, MB, csize):
     """The kernel's compile-time geometry of a shape (the same rules as its Geo template):
-    P in registers, CTAs per SM, y-pass sharing, plane buffers per group and the shared
-    memory of the plane buffers.  csize = bytes of one complex element."""
+    P in registers, CTAs per SM, y-pass sharing, tensor-memory accumulators, plane buffers per
+    group and the shared memory of the plane buffers.  csize = bytes of one complex element."""
     preg = (csize == 8 and N <= 48) or N <= 16
     buf = N * (N + 1) * csize
     threads = GP * N
@@ -95,8 +95,13 @@ def geometry(N, C, GP, MB, csize):
     else:
         res = 2 if threads <= 128 and 2 * (GP * 2 * buf + 1024) <= 228 * 1024 else 1
     ysh = N <= 16 and preg and res * (GP * 3 * buf + 1024 + 8 * 1024) <= 228 * 1024
-    nbuf = 2 if preg and not ysh else 3
-    return {"preg": preg, "res": res, "ysh": ysh, "nbuf": nbuf, "threads": threads,
+    # tensor-memory accumulators: P of the group's planes and a_e in 2N FP32 columns per line
+    ppg = (N // C) // GP
+    tm_cols = 2 * N * (ppg + 1)
+    tm_alloc = next(a for a in (32, 64, 128, 256, 512, 1 << 30) if tm_cols <= a)
+    tm = csize == 8 and N % 32 == 0 and threads <= 128 and not ysh and tm_cols <= 512 and res * tm_alloc <= 512
+    nbuf = 1 if tm else 2 if preg and not ysh else 3
+    return {"preg": preg, "res": res, "ysh": ysh, "tm": tm, "nbuf": nbuf, "threads": threads,
             "smem": GP * nbuf * buf}
 
 

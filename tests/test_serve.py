@@ -75,9 +75,11 @@ def test_chunked_srpt_lets_small_requests_overtake_a_large_one():
     """Chunked mode: a large request admitted first is split into chunks, and a small request
     that arrives later finishes long before it (FIFO whole-request service would finish it
     after the large one); every node of every request is submitted exactly once."""
-    fake = serve.FakeExecutor(seconds_per_node=2e-5)
+    # wall-clock timing: the large request takes 200 ms, so a few ms of thread-scheduling jitter
+    # on a loaded host stays well inside the margin
+    fake = serve.FakeExecutor(seconds_per_node=5e-5)
     big = serve.Request(0, 0.0, 16, 6.0, (1.0, 2.0), 0.7, 12, 8, 4000)
-    small = serve.Request(1, 0.01, 16, 6.0, (1.0, 3.0), 0.7, 12, 8, 20)
+    small = serve.Request(1, 0.02, 16, 6.0, (1.0, 3.0), 0.7, 12, 8, 20)
     eng = serve.ServingEngine(fake, budget_bytes=1 << 40, slots=1, chunk_s=0.005, policy="srpt")
     st = eng.run([big, small])
     assert small.done < big.done

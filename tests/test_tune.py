@@ -39,6 +39,13 @@ def test_geometry_mirrors_the_kernel_rules():
     assert g32["smem"] == 4 * 2 * 32 * 33 * 8   # 66 KB of plane buffers per CTA
     # P in shared memory: three buffers per group
     assert tune.geometry(32, 4, 4, 1, 16)["nbuf"] == 3
+    # tensor-memory accumulators: one plane per group in 8-CTA clusters at 3 CTAs per SM
+    # (3 x 128 of the 512 columns) keep only the transpose buffer; four planes per group
+    # (2-CTA clusters) would need 320 columns a CTA, so that shape keeps P in registers
+    g = tune.geometry(32, 8, 4, 3, 8)
+    assert g["tm"] and g["nbuf"] == 1 and g["smem"] == 4 * 32 * 33 * 8
+    assert not tune.geometry(32, 2, 4, 1, 8)["tm"] and tune.geometry(32, 4, 4, 2, 8)["tm"]
+    assert not tune.geometry(32, 8, 4, 3, 16)["tm"] and not tune.geometry(48, 4, 4, 1, 8)["tm"]
 
 
 def test_shape_line_round_trip():

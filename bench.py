@@ -56,7 +56,7 @@ def flops_per_transform(N):
 
 
 # the sources that define the collision kernel's code and launch shape
-COLLISION_KERNEL_SOURCES = ("collision_kernel.cuh", "fft_line.cuh", "collision_f32.cu", "collision_f64.cu",
+COLLISION_KERNEL_SOURCES = ("collision_kernel.cuh", "fft_line.cuh", "tcgen05.cuh", "collision_f32.cu", "collision_f64.cu",
                             "dgfs_internal.h", "tuned_shapes.h", "tuned_radix.h")
 
 

@@ -100,7 +100,10 @@ struct Geo {
   // Buffers of the shifted-volume pair: three for clusters of several CTAs, whose VHS phases
   // split the cluster barrier (a CTA arrives when its step A is written and waits at the end
   // of the phase, so a CTA may still read pair k-1 while another writes pair k+1), two otherwise.
-  static constexpr int NBV = CL > 1 ? 3 : 2;
+  // Measured at N = 32: 2-CTA clusters 2.6 % faster with the split; the TMEM shape (8-CTA
+  // clusters) as fast without it, and the third buffer raised its DRAM traffic from 28 to 45 GB
+  // per 288-node launch (L2 hit rate 86 % -> 74 %), so TMEM shapes keep two.
+  static constexpr int NBV = CL > 1 && !TM ? 3 : 2;
   // workspace volumes per cluster: f_hat_i, f_hat_j, the NBV pairs of shifted volumes, two P
   // volumes (the second used by the VSS pipeline), two gain accumulators
   static constexpr int SLOT = 2 + 2 * NBV + 4;
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THREADS, Geo<T, N>::MINB) collision
       // Pair k is written in phase k and read in phase k + 1, so with three buffers the pair
       // written in phase k + 1 is one that no CTA reads after arriving in phase k.  The VSS
       // pipeline's step B writes P volumes other CTAs read in the next phase: one full barrier.
-      const bool split = CL > 1 && !vss;
+      const bool split = G::NBV == 3 && !vss;
       const int nbv = split ? 3 : 2;
       for (int k = 0; k < n_phase; ++k) {
         if constexpr (G::STAGE) {

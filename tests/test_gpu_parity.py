@@ -29,6 +29,7 @@ CASES = {
     "radix3_n24_batch3": (24, 6.0, (1.0, 4.0), 0.5, 12, 4, 3),
     "three_species_n12": (12, 5.0, (1.0, 1.5, 2.6), 0.74, 12, 4, 2),
     "n32_single": (32, 7.0, (1.0, 2.1), 0.81, 6, 4, 1),
+    "n32_three_species_batch2": (32, 7.0, (1.0, 1.5, 2.6), 0.74, 6, 2, 2),
     "n8_batch5": (8, 4.0, (1.0, 3.0), 0.6, 6, 3, 5),
     "n6_three_species": (6, 4.0, (1.0, 2.0, 4.0), 0.9, 6, 2, 2),
     "n4_single_species": (4, 3.0, (1.0,), 0.7, 12, 2, 3),

@@ -28,6 +28,8 @@ CASES = {
     "n12_three_species_icosahedron": dict(N=12, L=5.0, masses=(1.0, 1.5, 2.6), omega=0.74, alpha=1.4, M=12, N_rho=3, B=2),
     "n16_m32_design": dict(N=16, L=6.0, masses=(1.0, 2.6), omega=0.74, alpha=1.4, M=32, N_rho=2, B=1),
     "n12_alpha2": dict(N=12, L=5.0, masses=(1.0, 3.0), omega=0.6, alpha=2.0, M=6, N_rho=3, B=2),
+    # N = 32 runs the FP32 tensor-memory shape (8-CTA clusters, dynamic pencil passes)
+    "n32_two_species": dict(N=32, L=7.0, masses=(1.0, 2.1), omega=0.81, alpha=1.4, M=6, N_rho=2, B=2),
 }
 
 

@@ -8,10 +8,10 @@ DGFS_RADIX(float, 4, 4)
 DGFS_RADIX(float, 6, 23)
 DGFS_RADIX(float, 8, 42)
 DGFS_RADIX(float, 12, 43)
-DGFS_RADIX(float, 16, 82)
+DGFS_RADIX(float, 16, 28)
 DGFS_RADIX(float, 24, 38)
 DGFS_RADIX(float, 32, 228)
-DGFS_RADIX(float, 48, 328)
+DGFS_RADIX(float, 48, 344)
 DGFS_RADIX(double, 4, 4)
 DGFS_RADIX(double, 6, 23)
 DGFS_RADIX(double, 8, 42)

@@ -10,7 +10,7 @@ DGFS_SHAPE(float, 12, 1, 12)
 DGFS_SHAPE3(float, 16, 1, 8, 3)
 DGFS_SHAPE3(float, 24, 1, 8, 2)
 DGFS_SHAPE3(float, 32, 8, 4, 3)
-DGFS_SHAPE3(float, 48, 4, 4, 1)
+DGFS_SHAPE3(float, 48, 2, 4, 1)
 DGFS_SHAPE(double, 4, 1, 4)
 DGFS_SHAPE(double, 6, 1, 6)
 DGFS_SHAPE(double, 8, 1, 8)

@@ -937,15 +937,28 @@ int configure_impl(Plan& pl) {
     return DGFS_ERR_CUDA;
   }
   if constexpr (G::TM) {
-    // The occupancy calculator grants a kernel that allocates tensor memory one CTA per SM.
-    // The registers, the shared memory and the TMEM columns (RES x TM_ALLOC <= 512) hold RES;
-    // clusters beyond what the device co-schedules wait, and the work counter leaves them the
-    // items still open when they start.
+    // The CTAs an SM can hold by the built kernel's registers, shared memory and threads must
+    // stay within the TMEM columns: a CTA that could not allocate would wait inside its
+    // cluster.  (The launch bounds size the registers for RES CTAs, whose allocations fit; a
+    // build with fewer registers could let more in.)
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return DGFS_ERR_CUDA;
+    const int warps = (G::THREADS + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? 65536 / (regs_warp * warps) : 32;
+    const int by_smem = int(size_t(228) * 1024 / (smem + fa.sharedSizeBytes + 1024));
+    int most = 2048 / G::THREADS;
+    if (by_regs < most) most = by_regs;
+    if (by_smem < most) most = by_smem;
+    if (most < 1 || most * G::TM_ALLOC > 512) return DGFS_ERR_CUDA;
+    // The occupancy calculator grants a kernel that allocates tensor memory one CTA per SM; the
+    // device co-schedules `most`.  Clusters beyond what it places wait, and the work counter
+    // leaves them the items still open when they start.
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return DGFS_ERR_CUDA;
-    const int cap = G::RES * sms / G::CL;
+    const int cap = most * sms / G::CL;
     if (cap > clusters) clusters = cap;
   }
   pl.shape.cluster = G::CL;

@@ -520,7 +520,8 @@ def gpu_arm(args):
     def step_e2e():
         plan32.eval_host(f_host, Q_host, stream)
 
-    ms_e2e = time_steps(torch, step_e2e, max(1, args.steps // 2), 1, stream, dist)
+    # the same warm-up and step counts as the device-resident measurement
+    ms_e2e = time_steps(torch, step_e2e, args.steps, max(3, args.warmup), stream, dist)
     e2e = {"value": world * B / (ms_e2e * 1e-3), "unit": "evals/s",
            "h2d_bytes_per_step": int(f_host.numel() * 4), "d2h_bytes_per_step": int(Q_host.numel() * 4)}
     del f_host, Q_host

@@ -2,6 +2,8 @@
 the same seeded inputs.  Bars: FP64 path <= 1e-11 max|Q| per node and pair; FP32 path
 <= 1e-5 of max|Q| over the node's s^2 operators (the mixed-precision target)."""
 
+import os
+
 import numpy as np
 import pytest
 
@@ -10,6 +12,7 @@ from oracle import fast_spectral as fs, krook_wu
 from paper_1903_03056_gb300 import build, dgfs, synth
 
 pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -114,21 +117,27 @@ def test_plan_radius_matches_domain_rule():
     plan.close()
 
 
-def test_krook_wu_exact_solution_on_gpu():
-    """Sum_j Q_ij from the FP64 GPU path against the exact d_t f of the Krook-Wu solution:
-    the error equals the oracle's (and Table 1's magnitude, N=32, N_rho=16, m1/m2=4)."""
-    N, L, ratio = 32, 12.0, 4.0
-    kw_sol = krook_wu.KrookWu(ratio, 1.0)
+@pytest.mark.parametrize("N,N_rho,ratio", [(32, 16, 4), (32, 8, 1), (16, 4, 8)])
+def test_krook_wu_exact_solution_on_gpu(N, N_rho, ratio):
+    """Sum_j Q_ij from the FP64 GPU path against the exact d_t f of the Krook-Wu solution, with
+    the radial truncation of Table 1 (R = 2S, S = 3, passed as the plan's radius): the errors
+    equal Table 1's printed values to within 0.3 %."""
+    L = 12.0
+    kw_sol = krook_wu.KrookWu(float(ratio), 1.0)
     v = fs.velocity_grid(N, L)
     vx, vy, vz = np.meshgrid(v, v, v, indexing="ij")
     v2 = vx * vx + vy * vy + vz * vz
     f = np.stack([kw_sol.f(0, 4.0, v2), kw_sol.f(1, 4.0, v2)])[None]
-    Q = gpu_collision(f, N=N, L=L, masses=(ratio, 1.0), omega=1.0, M=6, N_rho=16,
+    Q = gpu_collision(f, N=N, L=L, masses=(float(ratio), 1.0), omega=1.0, M=6, N_rho=N_rho, R=6.0,
                       precision="fp64", b_override=kw_sol.kernel_prefactors())
     err = [np.max(np.abs(Q[0, i].sum(axis=0) - kw_sol.df(i, 4.0, v2))) for i in range(2)]
-    paper = (8.018e-03, 9.020e-04)
+    col = {1: 0, 2: 2, 4: 4, 6: 6, 8: 8}[ratio]
+    with open(os.path.join(GOLDEN, "krook_wu_table1.txt")) as fh:
+        rows = {tuple(int(x) for x in line.split()[:2]): [float(x) for x in line.split()[2:]]
+                for line in fh if not line.startswith("#") and not line.startswith("N ")}
+    paper = rows[(N, N_rho)][col:col + 2]
     for e, p in zip(err, paper):
-        assert 0.5 < e / p < 2.0
+        assert abs(e / p - 1.0) < 3e-3, (err, paper)
 
 
 def test_batch_zero_and_bad_pointers():

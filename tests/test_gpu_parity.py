@@ -117,11 +117,13 @@ def test_plan_radius_matches_domain_rule():
     plan.close()
 
 
-@pytest.mark.parametrize("N,N_rho,ratio", [(32, 16, 4), (32, 8, 1), (16, 4, 8)])
-def test_krook_wu_exact_solution_on_gpu(N, N_rho, ratio):
-    """Sum_j Q_ij from the FP64 GPU path against the exact d_t f of the Krook-Wu solution, with
-    the radial truncation of Table 1 (R = 2S, S = 3, passed as the plan's radius): the errors
-    equal Table 1's printed values to within 0.3 %."""
+@pytest.mark.parametrize("N,N_rho,ratio,precision", [(32, 16, 4, "fp64"), (32, 8, 1, "fp64"), (16, 4, 8, "fp64"),
+                                                     (32, 16, 4, "fp32"), (32, 8, 1, "fp32"), (16, 8, 2, "fp32")])
+def test_krook_wu_exact_solution_on_gpu(N, N_rho, ratio, precision):
+    """Sum_j Q_ij from the GPU path against the exact d_t f of the Krook-Wu solution, with the
+    radial truncation of Table 1 (R = 2S, S = 3, passed as the plan's radius): the errors equal
+    Table 1's printed values to within 0.3 %, in FP64 and in FP32 (whose rounding, ~1e-6 of
+    max |Q|, is far below these errors)."""
     L = 12.0
     kw_sol = krook_wu.KrookWu(float(ratio), 1.0)
     v = fs.velocity_grid(N, L)
@@ -129,7 +131,7 @@ def test_krook_wu_exact_solution_on_gpu(N, N_rho, ratio):
     v2 = vx * vx + vy * vy + vz * vz
     f = np.stack([kw_sol.f(0, 4.0, v2), kw_sol.f(1, 4.0, v2)])[None]
     Q = gpu_collision(f, N=N, L=L, masses=(float(ratio), 1.0), omega=1.0, M=6, N_rho=N_rho, R=6.0,
-                      precision="fp64", b_override=kw_sol.kernel_prefactors())
+                      precision=precision, b_override=kw_sol.kernel_prefactors())
     err = [np.max(np.abs(Q[0, i].sum(axis=0) - kw_sol.df(i, 4.0, v2))) for i in range(2)]
     col = {1: 0, 2: 2, 4: 4, 6: 6, 8: 8}[ratio]
     with open(os.path.join(GOLDEN, "krook_wu_table1.txt")) as fh:

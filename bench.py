@@ -73,8 +73,8 @@ def kernel_sources_sha1():
 
 
 def hbm_peak_gbs():
-    """Measured HBM copy bandwidth of the GB300s (generated file), else the
-    earlier measurement on a GB300."""
+    """HBM copy bandwidth from the measured-peaks file beside this script (a STREAM-style copy
+    measured on this GPU model), else an earlier copy measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"

@@ -379,9 +379,9 @@ def _table1():
 
 
 # Radial truncation of the Krook-Wu runs: R = 2S (Sec. 4) with S = 3, the radius of the ball
-# the solution at t = 4 is taken to live in.  Eq. domain is then the condition on the box:
-# [-12, 12]^3 satisfies it for every mass ratio of Table 1 (at m1/m2 = 8 it needs 2L >= 22.7).
-# With this S the oracle gives every entry of Table 1 that is computed here to within 0.1 %.
+# the solution at t = 4 is taken to live in.  Eq. domain is then the condition on the velocity
+# domain: [-12, 12]^3 satisfies it for every mass ratio of Table 1 (at m1/m2 = 8 it needs
+# 2L >= 22.7).  With this S the oracle gives every entry of Table 1 computed here to within 0.1 %.
 KW_SUPPORT = 3.0
 
 
@@ -418,8 +418,9 @@ def test_krook_wu_reproduces_table1(N, N_rho, ratio):
 
 
 def test_krook_wu_truncation_reading_is_what_matches():
-    """The largest support the box permits (S = 2L / (3 + sqrt 2) = 5.44 for equal masses,
-    R = 10.9) misses Table 1's equal-mass N_rho = N/4 entry by 2.6x: the table fixes S = 3."""
+    """The largest support the velocity domain permits (S = 2L / (3 + sqrt 2) = 5.44 for equal
+    masses, R = 10.9) misses Table 1's equal-mass N_rho = N/4 entry by 2.6x: the table fixes
+    S = 3."""
     from oracle import kernel
     S_max = kernel.support_radius(12.0, np.array([1.0, 1.0]))
     got = krook_wu_errors(1, 16, 4, S=S_max)[0]

@@ -53,8 +53,10 @@ extern "C" {
 #define DGFS_ERR_CUDA (-5)           /* a CUDA runtime call or kernel launch failed */
 #define DGFS_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up: the DGFS_BF16X3
                                         kernel waits at most about one second for each batch
-                                        of its tensor-core MMAs, then stops and records it;
-                                        reported by dgfs_plan_check and dgfs_dft3_bf16x3 */
+                                        of its tensor-core MMAs, the FP32 collision kernel
+                                        (N = 24, 48) for each staged plane copy, then they
+                                        stop and record it; reported by dgfs_plan_check and
+                                        dgfs_dft3_bf16x3 */
 #define DGFS_ERR_UNSUPPORTED (-7)    /* a valid request this build does not implement */
 
 /* arithmetic of the transforms, products and accumulations */
@@ -117,7 +119,10 @@ typedef struct {
  * for N outside the list of the N field; DGFS_ERR_INVALID_ARG for a field outside its stated range,
  * a non-finite mass, b_ij, kappa, weight or R, a direction that is not a unit vector, an
  * unknown flag, or R > 0 with DGFS_PER_PAIR_R.  DGFS_ERR_OOM when the tables or the
- * workspace do not fit. */
+ * workspace do not fit.  DGFS_ERR_CUDA when a CUDA call fails, or when the collision kernel
+ * of a shape that keeps its accumulators in tensor memory (FP32, N = 32) could be placed
+ * more times per SM than the SM's 512 tensor-memory columns allow (judged from the built
+ * kernel's registers and shared memory; such a CTA would wait inside its cluster). */
 int dgfs_create_plan(const dgfs_plan_desc* desc, dgfs_plan* out);
 
 /* Release the plan's device memory.  Waits for the plan's most recent evaluation (not for
